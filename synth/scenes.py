@@ -1,0 +1,286 @@
+"""Workload builders: frame pairs, stereo sequences and camera-stream mixes.
+
+* ``make_config1``: one 752x480 mono pair.  Frame 2 is the continuous texture
+  seen through a 1 degree rotation about the image centre plus a seeded
+  sub-pixel translation |t| <= 8 px, evaluated exactly (no resampling); the
+  ground-truth position of every keypoint is known in closed form.
+* ``HeightFieldScene`` / ``make_stereo_sequence``: a textured wall whose depth
+  is a tilted plane at 2-5 m plus seeded Gaussian bumps, seen by a calibrated
+  stereo pair (baseline 0.11 m, f = 460 px at 752x480) moving at <= 0.3 m/s
+  (20 Hz) and rotating <= 5 degrees per frame.  Rays are cast per pixel on the
+  CPU (fixed-point iteration on the depth field); the texture is a raster
+  sampled with cubic B-spline interpolation.  The optional motion blur and
+  exposure change give the 1280x1024 precision-variant workload.
+* ``make_stream_mix`` / ``render_stream_frames``: independent camera streams of
+  uneven shapes (640x480, 752x480, 960x600, 1440x1080, 1920x1200), mono or
+  stereo, 200-2000 keypoints and 4-6 pyramid levels each, with frames related
+  by small rigid motions of an exactly evaluated texture.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import ndimage
+
+from .keypoints import select_keypoints_nms, select_keypoints_topfrac
+from .texture import BlobTexture, affine_from_motion, invert_affine, quantize_u8
+
+IDENTITY = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+
+
+# --------------------------------------------------------------------- config 1
+@dataclass
+class Config1Pair:
+    I: np.ndarray  # uint8 [h, w], previous frame
+    J: np.ndarray  # uint8 [h, w], current frame
+    pts: np.ndarray  # float32 [n, 2] keypoints in I
+    gt: np.ndarray  # float64 [n, 2] exact positions of the keypoints in J
+    motion: np.ndarray  # 2x3 rigid motion I -> J
+    seed: int
+    params: dict = field(default_factory=dict)
+
+
+def make_config1(seed: int = 1, w: int = 752, h: int = 480, n: int = 150, theta_deg: float = 1.0,
+                 max_shift: float = 8.0, margin: float = 28.0) -> Config1Pair:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tex = BlobTexture(seed * 7919 + 1, extent=(-60.0, -60.0, w + 60.0, h + 60.0))
+    I = quantize_u8(tex.eval_affine(w, h, IDENTITY))
+    # |t| <= max_shift: radius and angle drawn separately (sub-pixel by construction)
+    r = rng.uniform(0.25 * max_shift, max_shift)
+    a = rng.uniform(0.0, 2.0 * np.pi)
+    tx, ty = r * np.cos(a), r * np.sin(a)
+    M = affine_from_motion(theta_deg, tx, ty, (w - 1) / 2.0, (h - 1) / 2.0)
+    J = quantize_u8(tex.eval_affine(w, h, invert_affine(M)))
+    pts = select_keypoints_topfrac(I, n, seed * 7919 + 2, margin=margin)
+    p = pts.astype(np.float64)
+    gt = p @ M[:, :2].T + M[:, 2]
+    return Config1Pair(I=I, J=J, pts=pts, gt=gt, motion=M, seed=seed,
+                       params=dict(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5, min_eig=1e-4))
+
+
+# ---------------------------------------------------------------- height field
+def _rot(yaw: float, pitch: float, roll: float) -> np.ndarray:
+    cy, sy = np.cos(yaw), np.sin(yaw)
+    cp, sp = np.cos(pitch), np.sin(pitch)
+    cr, sr = np.cos(roll), np.sin(roll)
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rx = np.array([[1, 0, 0], [0, cp, -sp], [0, sp, cp]])
+    Rz = np.array([[cr, -sr, 0], [sr, cr, 0], [0, 0, 1]])
+    return Ry @ Rx @ Rz
+
+
+class HeightFieldScene:
+    """Textured wall Z = D(X, Y) in front of a moving stereo camera.
+
+    World axes follow the camera convention (X right, Y down, Z forward)."""
+
+    TEXEL_M = 0.0087  # one texture pixel, about one image pixel at 4 m and f = 460
+    OVERSAMPLE = 2  # raster cells per texture pixel
+    EXTENT = (-8.0, -6.0, 8.0, 6.0)  # metres
+
+    def __init__(self, seed: int, n_bumps: int = 40):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        x0, y0, x1, y1 = self.EXTENT
+        self.z0 = rng.uniform(3.0, 4.0)
+        self.sx = rng.uniform(-0.12, 0.12)
+        self.sy = rng.uniform(-0.12, 0.12)
+        # bumps: separable Gaussians, rastered at 2 cm and sampled with cubic splines
+        bx = rng.uniform(x0, x1, n_bumps)
+        by = rng.uniform(y0, y1, n_bumps)
+        bs = rng.uniform(0.2, 0.8, n_bumps)
+        ba = rng.uniform(-0.35, 0.35, n_bumps)
+        self.bump_res = 0.02
+        gxs = np.arange(x0, x1 + 1e-9, self.bump_res)
+        gys = np.arange(y0, y1 + 1e-9, self.bump_res)
+        Gx = np.exp(-((gxs[:, None] - bx) ** 2) / (2 * bs**2))
+        Gy = np.exp(-((gys[:, None] - by) ** 2) / (2 * bs**2))
+        bumps = (Gy * ba) @ Gx.T
+        self.bump_coef = ndimage.spline_filter(bumps, order=3, mode="nearest")
+        # wall texture in texture pixels; blob density matches 400 per 752x480
+        tw = (x1 - x0) / self.TEXEL_M
+        th = (y1 - y0) / self.TEXEL_M
+        n_blobs = int(round(400 * tw * th / (752 * 480)))
+        tex = BlobTexture(seed * 104729 + 3, extent=(0.0, 0.0, tw, th), n_blobs=n_blobs)
+        k = self.OVERSAMPLE
+        rw, rh = int(np.ceil(tw * k)), int(np.ceil(th * k))
+        raster = tex.eval_affine(rw, rh, np.array([[1.0 / k, 0, 0], [0, 1.0 / k, 0]]))
+        self.tex_coef = ndimage.spline_filter(raster, order=3, mode="nearest")
+        self.base = tex.base
+
+    def depth(self, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+        x0, y0, _, _ = self.EXTENT
+        bi = ndimage.map_coordinates(
+            self.bump_coef, [(Y - y0) / self.bump_res, (X - x0) / self.bump_res],
+            order=3, mode="nearest", prefilter=False)
+        return self.z0 + self.sx * X + self.sy * Y + bi
+
+    def render(self, R: np.ndarray, C: np.ndarray, w: int, h: int, f: float, iters: int = 10):
+        """Float image [h, w] and depth map seen by a pinhole camera (R, C)."""
+        cx, cy = (w - 1) / 2.0, (h - 1) / 2.0
+        xs = (np.arange(w) - cx) / f
+        ys = (np.arange(h) - cy) / f
+        dc = np.stack(np.broadcast_arrays(xs[None, :], ys[:, None], np.ones((h, w))), axis=-1)
+        d = dc @ R.T
+        dx, dy, dz = d[..., 0], d[..., 1], d[..., 2]
+        t = (self.z0 - C[2]) / dz
+        for _ in range(iters):
+            X = C[0] + t * dx
+            Y = C[1] + t * dy
+            t = (self.depth(X, Y) - C[2]) / dz
+        X = C[0] + t * dx
+        Y = C[1] + t * dy
+        x0, y0, _, _ = self.EXTENT
+        k = self.OVERSAMPLE / self.TEXEL_M
+        img = ndimage.map_coordinates(self.tex_coef, [(Y - y0) * k, (X - x0) * k], order=3,
+                                      mode="constant", cval=self.base, prefilter=False)
+        return img, t * dz
+
+
+def _motion_blur(img: np.ndarray, length: float, angle: float) -> np.ndarray:
+    if length < 1.0:
+        return img
+    n = 64
+    s = np.linspace(-0.5, 0.5, n) * length
+    xs = np.rint(s * np.cos(angle)).astype(int)
+    ys = np.rint(s * np.sin(angle)).astype(int)
+    r = int(np.ceil(length / 2.0)) + 1
+    k = np.zeros((2 * r + 1, 2 * r + 1))
+    np.add.at(k, (ys + r, xs + r), 1.0)
+    k /= k.sum()
+    return ndimage.convolve(img, k, mode="nearest")
+
+
+@dataclass
+class StereoSequence:
+    left: list  # uint8 [h, w] per frame
+    right: list
+    depth: list  # float32 depth of the left camera per frame
+    kps: list  # float32 [n, 2] per frame, on the left image
+    poses: list  # (R, C) of the left camera
+    f: float
+    baseline: float
+    seed: int
+    gains: list
+
+
+def make_stereo_sequence(seed: int = 2, n_frames: int = 4, w: int = 752, h: int = 480, n_kp: int = 1000,
+                         f: float | None = None, baseline: float = 0.11, fps: float = 20.0,
+                         max_speed: float = 0.3, max_rot_deg: float = 5.0, blur_max: float = 0.0,
+                         gain_range: tuple[float, float] | None = None, nms_radius: int = 4,
+                         scene: HeightFieldScene | None = None) -> StereoSequence:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if f is None:
+        f = 460.0 * w / 752.0
+    scene = scene or HeightFieldScene(seed)
+    # smooth trajectory: per-axis sinusoids, peak speed <= max_speed and
+    # peak rotation rate <= max_rot_deg per frame (split over three axes)
+    per_axis_v = max_speed / fps / np.sqrt(3.0)
+    per_axis_w = np.deg2rad(max_rot_deg) / np.sqrt(3.0)
+    Pt = rng.uniform(40.0, 120.0, 3)
+    vt = rng.uniform(0.3, 1.0, 3) * per_axis_v
+    pht = rng.uniform(0, 2 * np.pi, 3)
+    Pr = rng.uniform(30.0, 90.0, 3)
+    wr = rng.uniform(0.3, 1.0, 3) * per_axis_w
+    phr = rng.uniform(0, 2 * np.pi, 3)
+    left, right, depth, kps, poses, gains = [], [], [], [], [], []
+    for k in range(n_frames):
+        C = vt * Pt / (2 * np.pi) * np.sin(2 * np.pi * k / Pt + pht)
+        ang = wr * Pr / (2 * np.pi) * np.sin(2 * np.pi * k / Pr + phr)
+        R = _rot(*ang)
+        CR = C + R @ np.array([baseline, 0.0, 0.0])
+        imL, dL = scene.render(R, C, w, h, f)
+        imR, _ = scene.render(R, CR, w, h, f)
+        g = 1.0
+        if blur_max > 0:
+            bl, ba = rng.uniform(0, blur_max), rng.uniform(0, np.pi)
+            imL = _motion_blur(imL, bl, ba)
+            imR = _motion_blur(imR, bl, ba)
+        if gain_range is not None and k > 0:
+            g = rng.uniform(*gain_range)
+        L8 = quantize_u8((imL - 128.0) * g + 128.0 if g != 1.0 else imL)
+        R8 = quantize_u8((imR - 128.0) * g + 128.0 if g != 1.0 else imR)
+        left.append(L8)
+        right.append(R8)
+        depth.append(dL.astype(np.float32))
+        kps.append(select_keypoints_nms(L8, n_kp, seed * 31 + k, radius=nms_radius))
+        poses.append((R, C))
+        gains.append(g)
+    return StereoSequence(left, right, depth, kps, poses, f, baseline, seed, gains)
+
+
+def make_config3_pair(seed: int = 3, n_frames: int = 2, w: int = 1280, h: int = 1024, n_kp: int = 2000):
+    """1280x1024 stereo sequence with motion blur (0-7 px) and exposure gain
+    U[0.7, 1.3] on every frame after the first."""
+    return make_stereo_sequence(seed=seed, n_frames=n_frames, w=w, h=h, n_kp=n_kp,
+                                blur_max=7.0, gain_range=(0.7, 1.3))
+
+
+# ----------------------------------------------------------------- stream mix
+STREAM_SHAPES = [(640, 480), (752, 480), (960, 600), (1440, 1080), (1920, 1200)]
+
+
+@dataclass
+class StreamSpec:
+    sid: int
+    w: int
+    h: int
+    stereo: bool
+    n_kp: int
+    levels: int
+    seed: int
+
+
+def make_stream_mix(n_streams: int, seed: int = 4, kp_range=(200, 2000), levels=(4, 5, 6)) -> list:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for s in range(n_streams):
+        w, h = STREAM_SHAPES[int(rng.integers(0, len(STREAM_SHAPES)))]
+        out.append(StreamSpec(sid=s, w=w, h=h, stereo=bool(rng.integers(0, 2)),
+                              n_kp=int(rng.integers(kp_range[0], kp_range[1] + 1)),
+                              levels=int(levels[int(rng.integers(0, len(levels)))]),
+                              seed=seed * 1009 + s))
+    return out
+
+
+@dataclass
+class StreamFrames:
+    spec: StreamSpec
+    left: list
+    right: list  # None entries for mono streams
+    kps: list  # keypoints on each left frame
+
+
+def render_stream_frames(spec: StreamSpec, n_frames: int = 4, max_shift: float = 6.0,
+                         max_rot_deg: float = 0.5) -> StreamFrames:
+    """Frames k = 0..n_frames-1 of one stream: texture under a random walk of
+    small rigid motions; the right camera of a stereo stream sees the same
+    texture shifted left by a constant seeded disparity (a fronto-parallel
+    plane) plus a small vertical misalignment below 0.5 px."""
+    rng = np.random.Generator(np.random.PCG64(spec.seed))
+    w, h = spec.w, spec.h
+    tex = BlobTexture(spec.seed * 7 + 11, extent=(-120.0, -120.0, w + 120.0, h + 120.0),
+                      n_blobs=int(round(400 * (w + 240) * (h + 240) / (752 * 480))), blob_radius_sigmas=4.0)
+    disp = rng.uniform(4.0, 24.0)
+    vmis = rng.uniform(-0.4, 0.4)
+    theta, tx, ty = 0.0, 0.0, 0.0
+    left, right, kps = [], [], []
+    for k in range(n_frames):
+        M = affine_from_motion(theta, tx, ty, (w - 1) / 2.0, (h - 1) / 2.0)
+        A = invert_affine(M)
+        L = quantize_u8(tex.eval_affine(w, h, A))
+        left.append(L)
+        if spec.stereo:
+            MR = np.array([[1.0, 0.0, -disp], [0.0, 1.0, vmis]])
+            AR = invert_affine(np.vstack([MR, [0, 0, 1]])[:2] @ np.vstack([M, [0, 0, 1]]))
+            right.append(quantize_u8(tex.eval_affine(w, h, AR)))
+        else:
+            right.append(None)
+        kps.append(select_keypoints_topfrac(L, spec.n_kp, spec.seed * 13 + k, margin=30.0, top_frac=0.3))
+        r = rng.uniform(0.3, 1.0) * max_shift
+        a = rng.uniform(0, 2 * np.pi)
+        tx += r * np.cos(a)
+        ty += r * np.sin(a)
+        theta += rng.uniform(-max_rot_deg, max_rot_deg)
+    return StreamFrames(spec, left, right, kps)
