@@ -1,0 +1,213 @@
+/*
+ * vt.h - pyramidal Lucas-Kanade (KLT) feature tracking on one GB300 GPU.
+ *
+ * The operation: the LK optical-flow front-end of DL-VINS-Factory tracks
+ * keypoints from the previous frame to the current one and, in stereo, from
+ * the left to the right image, keeping only features that pass a
+ * cross-camera optical-flow check (Sec. IV: Shi-Tomasi corners with LK
+ * optical flow as the classical front-end; Sec. III-A: LK tracking needs
+ * keypoints only, so any extractor's keypoints P in R^{N x 2} of Eq. 1 can
+ * feed it; Table I: the KLT tracker inherited from VINS-Fusion; Sec. V-A:
+ * stereo features enter the temporal pool only after the cross-camera flow
+ * check).  The paper fixes none of the tracker's constants; the readings this
+ * library implements are stated beside each call.
+ *
+ * Conventions for every call:
+ *   - Plain C ABI: pointers and sizes only.  "device" pointers are CUDA
+ *     global-memory addresses valid on the current device; "host" pointers
+ *     are ordinary (preferably pinned) host memory.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Every
+ *     call is asynchronous on that stream unless stated otherwise; results
+ *     are visible after the stream is synchronised.
+ *   - Images are 8-bit grey, row-major, `pitch` bytes between rows.
+ *   - Points are float2 (x, y) in level-0 pixels; pixel centres sit at
+ *     integer coordinates.
+ *   - Errors are returned, never thrown: VT_ERR_ARG for a bad argument
+ *     (nothing is launched), VT_ERR_OOM when device memory runs out,
+ *     VT_ERR_CUDA when a CUDA call or launch fails (the stream may hold
+ *     partial work).  Per-point failures are reported in `status`.
+ *   - Ownership: the caller owns every point / status / error buffer; the
+ *     library owns pyramids (vt_pyramid_free releases them).
+ */
+#ifndef VT_H
+#define VT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VT_API __attribute__((visibility("default")))
+#else
+#define VT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vt_status {
+    VT_OK = 0,
+    VT_ERR_ARG = 1,
+    VT_ERR_OOM = 2,
+    VT_ERR_CUDA = 3,
+    VT_ERR_TIMEOUT = 4,
+    VT_ERR_UNSUPPORTED = 5
+} vt_status;
+
+/* Gradient storage of a pyramid. */
+typedef enum vt_grad_type {
+    VT_GRAD_NONE = 0,
+    VT_GRAD_S16 = 1, /* raw Scharr as int16 pairs (dx, dy), range [-4080, 4080] */
+    VT_GRAD_F16 = 2  /* raw / 32 as half pairs, round to nearest even */
+} vt_grad_type;
+
+/* Per-point reason codes (optional diagnostics). */
+enum {
+    VT_TRACKED = 0,
+    VT_LOST_EIG = 1,   /* lambda_min(G) below threshold, or det(G) <= 0 */
+    VT_LOST_OOB = 2,   /* estimate left the image (see vt_klt_track) */
+    VT_LOST_FB = 3,    /* forward-backward distance above threshold */
+    VT_LOST_INPUT = 4  /* input point outside [0, W-1] x [0, H-1] or NaN */
+};
+
+enum { VT_MAX_LEVELS = 8 };      /* levels per pyramid */
+#define VT_DEFAULT_MIN_EIG 1e-4f /* threshold on lambda_min(G) / (win^2 * 255^2) */
+
+/* Window sides the tracking kernels are built for. */
+#define VT_SUPPORTED_WINDOWS {9, 15, 21, 31}
+
+typedef struct vt_pyramid vt_pyramid; /* opaque, device-resident, owned by the library */
+
+/*
+ * vt_pyramid_build - Gaussian image pyramid (the coarse-to-fine pyramid of
+ * the LK tracker, Sec. IV; its filter is unstated in the paper).
+ *
+ * Level 0 is a copy of `img` (w x h, `pitch` bytes per row; a host pointer
+ * when img_on_device == 0, else a device pointer).  Level l+1 has size
+ * ceil(w_l / 2) x ceil(h_l / 2) and is the 5x5 separable [1 4 6 4 1]^2 / 256
+ * sum centred at (2x, 2y) of level l, reflect-101 borders (clamp on a 1-px
+ * side), rounded as (s + 128) >> 8: bit-exact integer arithmetic.
+ *
+ * levels: 1..VT_MAX_LEVELS (ceil-halving keeps every level >= 1x1; 1-px levels
+ * repeat).  VT_ERR_ARG for w, h <= 0, pitch < w or levels out of range.
+ * *out == NULL: a new pyramid is allocated (one cudaMalloc) and returned.
+ * *out != NULL: it must have been built with the same w, h and levels; it is
+ *   rebuilt in place without allocating (VT_ERR_ARG on a mismatch).
+ * Gradients of a rebuilt pyramid are stale until vt_gradients is called.
+ */
+VT_API vt_status vt_pyramid_build(const uint8_t *img, int w, int h, int pitch, int levels, int img_on_device,
+                           void *cuda_stream, vt_pyramid **out);
+
+/*
+ * vt_gradients - Scharr derivatives of every level of `p`:
+ *   dx = [-3 0 3; -10 0 10; -3 0 3] * I,  dy = its transpose,
+ * reflect-101 borders, stored as (dx, dy) pairs per pixel: raw int16
+ * (VT_GRAD_S16, bit-exact) or raw / 32 rounded to half (VT_GRAD_F16).
+ * raw / 32 is the derivative in grey levels per pixel.
+ */
+VT_API vt_status vt_gradients(vt_pyramid *p, vt_grad_type t, void *cuda_stream);
+
+/*
+ * vt_pyramid_build_grad - vt_pyramid_build followed by vt_gradients in one
+ * pass over each level (level l's gradients are computed from the same
+ * staged tile that produces level l+1).  Same arguments and results.
+ */
+VT_API vt_status vt_pyramid_build_grad(const uint8_t *img, int w, int h, int pitch, int levels, int img_on_device,
+                                vt_grad_type t, void *cuda_stream, vt_pyramid **out);
+
+/* Level `lvl` of `p`: device image pointer, size and pitch (bytes). */
+VT_API vt_status vt_pyramid_level(const vt_pyramid *p, int lvl, const uint8_t **ptr, int *w, int *h, int *pitch);
+
+/* Gradient plane of level `lvl`: device pointer to (dx, dy) pairs, pitch in
+ * pairs, storage type (VT_GRAD_NONE before vt_gradients). */
+VT_API vt_status vt_pyramid_grad(const vt_pyramid *p, int lvl, const void **ptr, int *pitch_pairs, vt_grad_type *t);
+
+/* Shape of `p`. */
+VT_API vt_status vt_pyramid_info(const vt_pyramid *p, int *w, int *h, int *levels, size_t *device_bytes);
+
+/* Frees `p` (synchronises the device first; NULL is ignored). */
+VT_API void vt_pyramid_free(vt_pyramid *p);
+
+/*
+ * vt_klt_track - pyramidal Lucas-Kanade from `prev` to `cur` (the
+ * prev->cur temporal tracking of the LK front-end; with prev = left and
+ * cur = right it is the cross-camera flow of Sec. V-A).
+ *
+ * Both pyramids need gradients (vt_gradients).  For each point u (float2,
+ * device, n entries), levels l = levels-1 .. 0, u_l = u / 2^l, window
+ * offsets x in [-h, h]^2 with h = win / 2:
+ *   T(x) = I_l(u_l + x) and grad T(x) bilinearly sampled (replicate-clamped
+ *   neighbours) from prev's level l image and gradient planes;
+ *   G = sum grad T grad T^T; the point is lost if lambda_min(G) / (win^2 255^2)
+ *   < min_eig (VT_DEFAULT_MIN_EIG here) or det(G) <= 0;
+ *   nu = 0; up to max_iters times: q = u_l + g_l + nu must lie in
+ *   [-h, w_l - 1 + h] x [-h, h_l - 1 + h] (else lost), r(x) = T(x) - J_l(q + x),
+ *   b = sum r grad T, eta = G^-1 b, nu += eta, stop when |eta|^2 < eps^2;
+ *   g_{l-1} = 2 (g_l + nu); g_{levels-1} = 0, or (guess - u) / 2^(levels-1)
+ *   when pts_guess (device, nullable) is given.
+ * The result v = u + g_0 + nu must lie in [0, W-1] x [0, H-1] (else lost).
+ * Outputs (device, caller-owned, n entries): pts_out = v (for a lost point:
+ * its last estimate, scaled to level 0), status = 1 tracked / 0 lost,
+ * err = mean |T(x) - J_0(v + x)| over the window (0 when lost; nullable).
+ * G, b and the residual are accumulated in FP32; the 2x2 solve falls back to
+ * FP64 when lambda_max / lambda_min > 1e5.
+ * win: one of VT_SUPPORTED_WINDOWS.  levels: 1..min(prev, cur levels).
+ * max_iters >= 1, eps >= 0.  n == 0 launches nothing.
+ */
+VT_API vt_status vt_klt_track(const vt_pyramid *prev, const vt_pyramid *cur, const float *pts_in, int n,
+                       const float *pts_guess, int win, int levels, int max_iters, float eps, float *pts_out,
+                       uint8_t *status, float *err, void *cuda_stream);
+
+/* Tracking parameters for the _ex / _fb / batched calls. */
+typedef struct vt_klt_params {
+    int win;       /* one of VT_SUPPORTED_WINDOWS */
+    int levels;    /* levels used */
+    int max_iters; /* Newton iterations per level, >= 1 */
+    float eps;     /* stop when |eta| < eps (level pixels) */
+    float min_eig; /* threshold on lambda_min(G) / (win^2 255^2) */
+    float fb_thr;  /* forward-backward threshold in level-0 pixels (fused calls) */
+} vt_klt_params;
+
+/* Optional per-point diagnostics (device arrays of n entries, each nullable). */
+typedef struct vt_klt_diag {
+    uint8_t *reason; /* VT_TRACKED / VT_LOST_* */
+    int32_t *iters;  /* Newton iterations summed over levels (forward pass) */
+    float *lmin;     /* normalised lambda_min of G at the last level examined */
+} vt_klt_diag;
+
+/* vt_klt_track with an explicit parameter block and diagnostics (diag nullable). */
+VT_API vt_status vt_klt_track_ex(const vt_pyramid *prev, const vt_pyramid *cur, const float *pts_in, int n,
+                          const float *pts_guess, const vt_klt_params *prm, float *pts_out, uint8_t *status,
+                          float *err, const vt_klt_diag *diag, void *cuda_stream);
+
+/*
+ * vt_fb_check - forward-backward consistency (the cross-camera / temporal
+ * flow check of Sec. V-A): status_out[i] = st_f[i] && st_b[i] &&
+ * |p0[i] - p0_back[i]|_2 <= thr (inclusive).  All arrays device, n entries.
+ */
+VT_API vt_status vt_fb_check(const float *p0, const float *p0_back, const uint8_t *st_f, const uint8_t *st_b, int n,
+                      float thr, uint8_t *status_out, void *cuda_stream);
+
+/*
+ * vt_klt_track_fb - forward track prev->cur, backward track cur->prev from
+ * the forward result, and vt_fb_check with prm->fb_thr, fused in one launch
+ * (one warp carries a point through both passes).  pts_out / err are the
+ * forward results; status is the forward-backward status; diag->reason
+ * gives the first failure (forward, then backward, then VT_LOST_FB).
+ * Identical to vt_klt_track_ex + vt_klt_track_ex + vt_fb_check.
+ */
+VT_API vt_status vt_klt_track_fb(const vt_pyramid *prev, const vt_pyramid *cur, const float *pts_in, int n,
+                          const vt_klt_params *prm, float *pts_out, uint8_t *status, float *err,
+                          const vt_klt_diag *diag, void *cuda_stream);
+
+/* Human-readable name of a status code. */
+VT_API const char *vt_status_str(vt_status s);
+
+/* Library version string and the device architecture it was built for. */
+VT_API const char *vt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VT_H */

@@ -1,0 +1,91 @@
+// Internal structures shared by the CUDA translation units of libvt.
+// Device-side layout of a pyramid, job tables and small device helpers.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vt.h"
+
+namespace vt {
+
+// One level as the kernels see it.  Images are uint8 with `pitch` bytes per
+// row (multiple of 64); gradients are 32-bit (dx, dy) pairs (int16x2 or
+// half2) with `gpitch` pairs per row (multiple of 32, i.e. 128-byte rows).
+struct Level {
+    uint8_t *img;
+    uint32_t *grad;
+    int w, h, pitch, gpitch;
+};
+
+}  // namespace vt
+
+struct vt_pyramid {
+    int w, h, levels;
+    int gtype;  // vt_grad_type of the current gradient planes
+    int device;
+    void *base;  // single device allocation holding every level and plane
+    size_t bytes;
+    vt::Level lv[VT_MAX_LEVELS];
+};
+
+namespace vt {
+
+constexpr int kImgPitchAlign = 64;
+constexpr int kGradPitchAlign = 32;
+
+inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Reflect-101 border index; a 1-px side clamps.
+__device__ __forceinline__ int refl101(int i, int n) {
+    if (n == 1) return 0;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * n - 2 - i;
+    }
+    return i;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// ---------------------------------------------------------------- pyramid jobs
+// A pyrDown (and optionally Scharr) job: level src (w x h) -> dst
+// (ceil(w/2) x ceil(h/2)); gradients of the src level when grad != nullptr.
+struct PyrJob {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint32_t *grad;
+    int w, h, spitch, dpitch, gpitch;
+    int tiles_x;  // output tiles along x
+    int tile0;    // first block of this job
+};
+
+constexpr int kMaxJobs = 48;
+
+struct PyrJobs {
+    int njobs;
+    PyrJob j[kMaxJobs];
+};
+
+// A Scharr-only job over one level.
+struct GradJob {
+    const uint8_t *src;
+    uint32_t *grad;
+    int w, h, spitch, gpitch;
+    int tiles_x;
+    int tile0;
+};
+
+struct GradJobs {
+    int njobs;
+    GradJob j[kMaxJobs];
+};
+
+// Host helpers implemented in vt_pyramid.cu.
+vt_status launch_pyrdown(const PyrJobs &jobs, int total_blocks, int gtype, cudaStream_t s);
+vt_status launch_scharr(const GradJobs &jobs, int total_blocks, int gtype, cudaStream_t s);
+void add_pyr_job(PyrJobs &jobs, int &blocks, const Level &src, const Level &dst, bool with_grad);
+void add_grad_job(GradJobs &jobs, int &blocks, const Level &lv);
+
+}  // namespace vt

@@ -1,0 +1,300 @@
+// Warp-per-feature pyramidal Lucas-Kanade (K3), shared by the single-pair
+// kernels (vt_klt.cu) and the batched persistent kernel (vt_batch.cu) so that
+// a point gives bit-identical results alone or in a batch.
+//
+// The method (textbook coarse-to-fine LK, the tracker the paper uses in
+// Sec. IV / Table I; cross-camera check of Sec. V-A):
+//   per level l = L-1 .. 0, u_l = u / 2^l:
+//     T(x), grad T(x): bilinear samples of I_l and its Scharr planes at u_l + x
+//     G = sum grad T grad T^T, reject if lambda_min / (win^2 255^2) < min_eig
+//     iterate: q = u_l + g_l + nu (bound test), r = T - J_l(q + x),
+//              b = sum r grad T, eta = G^-1 b, nu += eta, stop |eta|^2 < eps^2
+//     g_{l-1} = 2 (g_l + nu)
+//   result v = u + g_0 + nu (bound test), error = mean |T - J_0(v + x)|.
+//
+// Mapping to the warp: lane c owns window column c for every row (lanes
+// c <= win load, lanes c < win compute).  Every window sample shares the
+// same fractional bilinear weights, so a row is one coalesced load of
+// win + 1 consecutive bytes, the right neighbour comes from the next lane by
+// shuffle and the vertical blend reuses the previous row.  The template and
+// its gradients stay in registers (3 * win floats per lane).  Sums over the
+// window are per-lane FP32 sums over rows followed by an XOR butterfly, so
+// every lane holds bit-identical totals and control flow stays warp-uniform.
+#pragma once
+
+#include "vt_internal.cuh"
+
+namespace vt {
+
+struct KPyr {
+    Level lv[VT_MAX_LEVELS];
+};
+
+struct KParams {
+    int win, levels, max_iters;
+    float eps2;     // eps^2
+    float min_eig;  // threshold on lambda_min / (win^2 255^2)
+    float fb_thr2;  // fb_thr^2
+};
+
+struct KOut {
+    float x, y;     // level-0 result (last estimate when lost)
+    float err;      // mean |T - J| (0 when lost)
+    float lmin;     // normalised lambda_min at the last level examined
+    int status;     // 1 tracked
+    int reason;     // VT_TRACKED / VT_LOST_*
+    int iters;      // Newton iterations over all levels
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+// 2^23 + v as a float for a byte v: differences of two such values are exact.
+__device__ __forceinline__ float magic_u8(uint32_t v) { return __uint_as_float(0x4B000000u | v); }
+constexpr float kMagic = 8388608.0f;
+
+template <int GT>
+__device__ __forceinline__ void unpack_grad(uint32_t v, float &gx, float &gy) {
+    if (GT == VT_GRAD_S16) {
+        gx = (float)(int)(int16_t)(v & 0xffffu);
+        gy = (float)((int)v >> 16);
+    } else {
+        const __half2 h = *reinterpret_cast<const __half2 *>(&v);
+        const float2 f = __half22float2(h);
+        gx = f.x;
+        gy = f.y;
+    }
+}
+
+// Scale from the stored gradient unit to grey levels per pixel.
+template <int GT>
+__device__ __forceinline__ constexpr float grad_unit() { return GT == VT_GRAD_S16 ? 0.03125f : 1.0f; }
+
+// 2^-l exactly.
+__device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
+
+// Sample the template (image and gradients) of level `L` around (ux, uy).
+// Lane c ends with column c of the window in T/GX/GY (zero for c >= WIN).
+template <int WIN, int GT>
+__device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
+                                              float (&GX)[WIN], float (&GY)[WIN]) {
+    constexpr int HW = WIN / 2;
+    const float fx = floorf(ux), fy = floorf(uy);
+    const float ax = ux - fx, ay = uy - fy;
+    const int x0 = (int)fx - HW, y0 = (int)fy - HW;
+    const int col = clampi(x0 + lane, 0, L.w - 1);
+    const uint8_t *ib = L.img + col;
+    const uint32_t *gb = L.grad + col;
+    const bool ld = lane <= WIN;
+    float pi = 0.f, pgx = 0.f, pgy = 0.f;
+#pragma unroll
+    for (int r = 0; r <= WIN; ++r) {
+        const int row = clampi(y0 + r, 0, L.h - 1);
+        uint32_t v = 0, g = 0;
+        if (ld) {
+            v = __ldg(ib + (size_t)row * L.pitch);
+            g = __ldg(gb + (size_t)row * L.gpitch);
+        }
+        const float mv = magic_u8(v);
+        const float mvr = __shfl_down_sync(kFull, mv, 1);
+        float gx, gy;
+        unpack_grad<GT>(g, gx, gy);
+        const float gxr = __shfl_down_sync(kFull, gx, 1);
+        const float gyr = __shfl_down_sync(kFull, gy, 1);
+        const float hi = fmaf(ax, mvr - mv, mv - kMagic);
+        const float hgx = fmaf(ax, gxr - gx, gx);
+        const float hgy = fmaf(ax, gyr - gy, gy);
+        if (r > 0) {
+            T[r - 1] = fmaf(ay, hi - pi, pi);
+            GX[r - 1] = fmaf(ay, hgx - pgx, pgx);
+            GY[r - 1] = fmaf(ay, hgy - pgy, pgy);
+        }
+        pi = hi;
+        pgx = hgx;
+        pgy = hgy;
+    }
+    if (lane >= WIN) {
+#pragma unroll
+        for (int r = 0; r < WIN; ++r) T[r] = GX[r] = GY[r] = 0.f;
+    }
+}
+
+// One pass over J_l at (qx, qy): b = sum r grad T (ABS = false) or
+// e = sum |r| over the window (ABS = true, returned in b1).
+template <int WIN, bool ABS>
+__device__ __forceinline__ void residual_pass(const Level &L, float qx, float qy, int lane, const float (&T)[WIN],
+                                              const float (&GX)[WIN], const float (&GY)[WIN], float &b1,
+                                              float &b2) {
+    constexpr int HW = WIN / 2;
+    const float fx = floorf(qx), fy = floorf(qy);
+    const float bx = qx - fx, by = qy - fy;
+    const int x0 = (int)fx - HW, y0 = (int)fy - HW;
+    const int col = clampi(x0 + lane, 0, L.w - 1);
+    const uint8_t *jb = L.img + col;
+    const bool ld = lane <= WIN;
+    float s1 = 0.f, s2 = 0.f, ph = 0.f;
+#pragma unroll
+    for (int r = 0; r <= WIN; ++r) {
+        const int row = clampi(y0 + r, 0, L.h - 1);
+        uint32_t v = 0;
+        if (ld) v = __ldg(jb + (size_t)row * L.pitch);
+        const float mv = magic_u8(v);
+        const float mvr = __shfl_down_sync(kFull, mv, 1);
+        const float h = fmaf(bx, mvr - mv, mv - kMagic);
+        if (r > 0) {
+            const float jv = fmaf(by, h - ph, ph);
+            const float res = T[r - 1] - jv;
+            if (ABS) {
+                s1 += (lane < WIN) ? fabsf(res) : 0.f;
+            } else {
+                s1 = fmaf(res, GX[r - 1], s1);
+                s2 = fmaf(res, GY[r - 1], s2);
+            }
+        }
+        ph = h;
+    }
+    b1 = warp_sum(s1);
+    if (!ABS) b2 = warp_sum(s2);
+}
+
+// Track one point u = (ux0, uy0) from pyramid I to pyramid J.
+template <int WIN, int GT>
+__device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
+                                            bool has_guess, float gux, float guy, int lane, KOut &o) {
+    constexpr int HW = WIN / 2;
+    constexpr float N = (float)(WIN * WIN);
+    constexpr float unit = grad_unit<GT>();
+    // lambda_min normalisation: stored units^2 -> (grey/px)^2, / (N 255^2)
+    const float inv_norm = unit * unit / (N * 65025.0f);
+    float T[WIN], GX[WIN], GY[WIN];
+    const int L = P.levels;
+    float gx = 0.f, gy = 0.f, nux = 0.f, nuy = 0.f;
+    int lost_level = 0;
+    o.status = 1;
+    o.reason = VT_TRACKED;
+    o.iters = 0;
+    o.err = 0.f;
+    o.lmin = __int_as_float(0x7fc00000);
+    if (!(ux0 >= 0.f && ux0 <= (float)(I[0].w - 1) && uy0 >= 0.f && uy0 <= (float)(I[0].h - 1))) {
+        o.status = 0;
+        o.reason = VT_LOST_INPUT;
+        o.x = ux0;
+        o.y = uy0;
+        return;
+    }
+    if (has_guess) {
+        const float s = pow2neg(L - 1);
+        gx = (gux - ux0) * s;
+        gy = (guy - uy0) * s;
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const Level &Il = I[l];
+        const Level &Jl = J[l];
+        const float s = pow2neg(l);
+        const float ux = ux0 * s, uy = uy0 * s;
+        load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY);
+        float a11 = 0.f, a12 = 0.f, a22 = 0.f;
+#pragma unroll
+        for (int r = 0; r < WIN; ++r) {
+            a11 = fmaf(GX[r], GX[r], a11);
+            a12 = fmaf(GX[r], GY[r], a12);
+            a22 = fmaf(GY[r], GY[r], a22);
+        }
+        const float g11 = warp_sum(a11), g12 = warp_sum(a12), g22 = warp_sum(a22);
+        // lambda_min = det / lambda_max avoids the cancellation of (tr - disc) / 2
+        const float tr = g11 + g22, df = g11 - g22;
+        const float lmax = 0.5f * (tr + sqrtf(fmaf(df, df, 4.f * g12 * g12)));
+        const double det = (double)g11 * (double)g22 - (double)g12 * (double)g12;
+        const float lmin = (float)(det / (double)lmax);
+        o.lmin = lmin * inv_norm;
+        nux = nuy = 0.f;
+        if (!(o.lmin >= P.min_eig) || !(det > 0.0)) {
+            o.status = 0;
+            o.reason = VT_LOST_EIG;
+            lost_level = l;
+            break;
+        }
+        // eta = G^-1 b in grey/px units: G = unit^2 G_s, b = unit b_s => eta = adj(G_s) b_s / (unit det_s)
+        const bool fp64 = lmax > 1e5f * lmin;
+        const float inv_det = (float)(1.0 / (det * (double)unit));
+        int k = 0;
+        for (; k < P.max_iters; ++k) {
+            const float qx = ux + gx + nux, qy = uy + gy + nuy;
+            const float dist = fminf(fminf(qx + (float)HW, (float)(Jl.w - 1 + HW) - qx),
+                                     fminf(qy + (float)HW, (float)(Jl.h - 1 + HW) - qy));
+            if (!(dist >= 0.f)) {
+                o.status = 0;
+                o.reason = VT_LOST_OOB;
+                break;
+            }
+            float b1, b2;
+            residual_pass<WIN, false>(Jl, qx, qy, lane, T, GX, GY, b1, b2);
+            float ex, ey;
+            if (!fp64) {
+                ex = (g22 * b1 - g12 * b2) * inv_det;
+                ey = (g11 * b2 - g12 * b1) * inv_det;
+            } else {
+                const double dd = det * (double)unit;
+                ex = (float)(((double)g22 * b1 - (double)g12 * b2) / dd);
+                ey = (float)(((double)g11 * b2 - (double)g12 * b1) / dd);
+            }
+            nux += ex;
+            nuy += ey;
+            ++o.iters;
+            if (ex * ex + ey * ey < P.eps2) break;
+        }
+        if (!o.status) {
+            lost_level = l;
+            break;
+        }
+        if (l > 0) {
+            gx = 2.f * (gx + nux);
+            gy = 2.f * (gy + nuy);
+        }
+    }
+    {
+        const float sc = (float)(1 << lost_level);
+        const float si = pow2neg(lost_level);
+        o.x = (ux0 * si + gx + nux) * sc;
+        o.y = (uy0 * si + gy + nuy) * sc;
+    }
+    if (o.status) {
+        const float dist = fminf(fminf(o.x, (float)(I[0].w - 1) - o.x), fminf(o.y, (float)(I[0].h - 1) - o.y));
+        if (!(dist >= 0.f)) {
+            o.status = 0;
+            o.reason = VT_LOST_OOB;
+        } else {
+            // T still holds level 0's template
+            float e, unused;
+            residual_pass<WIN, true>(J[0], o.x, o.y, lane, T, GX, GY, e, unused);
+            o.err = e / N;
+        }
+    }
+}
+
+// Forward I->J, backward J->I from the forward result, FB test.
+template <int WIN, int GT>
+__device__ __forceinline__ void track_point_fb(const Level *I, const Level *J, const KParams &P, float ux0,
+                                               float uy0, int lane, KOut &o) {
+    track_point<WIN, GT>(I, J, P, ux0, uy0, false, 0.f, 0.f, lane, o);
+    if (!o.status) return;
+    KOut b;
+    track_point<WIN, GT>(J, I, P, o.x, o.y, false, 0.f, 0.f, lane, b);
+    if (!b.status) {
+        o.status = 0;
+        o.reason = b.reason;
+        return;
+    }
+    const float dx = ux0 - b.x, dy = uy0 - b.y;
+    if (!(dx * dx + dy * dy <= P.fb_thr2)) {
+        o.status = 0;
+        o.reason = VT_LOST_FB;
+    }
+}
+
+}  // namespace vt

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libvt (include/vt.h).
+
+Argument marshalling only: every step of the tracking path runs in the CUDA
+library.  Functions carry the C names; tensors are torch tensors on the GPU
+(their ``data_ptr``), images may also be host numpy / CPU torch arrays for the
+``vt_pyramid_build*`` calls.  There is no CPU fallback: importing this module
+raises if libvt.so cannot be loaded.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+
+from . import build as _build
+
+VT_OK, VT_ERR_ARG, VT_ERR_OOM, VT_ERR_CUDA, VT_ERR_TIMEOUT, VT_ERR_UNSUPPORTED = range(6)
+VT_GRAD_NONE, VT_GRAD_S16, VT_GRAD_F16 = 0, 1, 2
+VT_TRACKED, VT_LOST_EIG, VT_LOST_OOB, VT_LOST_FB, VT_LOST_INPUT = range(5)
+VT_MAX_LEVELS = 8
+VT_DEFAULT_MIN_EIG = 1e-4
+SUPPORTED_WINDOWS = (9, 15, 21, 31)
+
+
+class VTError(RuntimeError):
+    def __init__(self, what: str, code: int):
+        super().__init__(f"{what}: {vt_status_str(code)}")
+        self.code = code
+
+
+def _load() -> C.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path) or _build.needs_build():
+        try:
+            path = _build.build()
+        except Exception as e:  # noqa: BLE001 - report why the library is unusable
+            raise ImportError(f"libvt.so is missing and could not be built ({e}); "
+                              "build it with: python -m paper_2607_01757_gb300.build") from e
+    return C.CDLL(path)
+
+
+_lib = _load()
+LIB_PATH = _lib._name
+
+vp, i32, f32 = C.c_void_p, C.c_int, C.c_float
+
+
+class vt_klt_params(C.Structure):
+    _fields_ = [("win", i32), ("levels", i32), ("max_iters", i32), ("eps", f32), ("min_eig", f32),
+                ("fb_thr", f32)]
+
+
+class vt_klt_diag(C.Structure):
+    _fields_ = [("reason", vp), ("iters", vp), ("lmin", vp)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("vt_pyramid_build", i32, [vp, i32, i32, i32, i32, i32, vp, C.POINTER(vp)])
+_sig("vt_pyramid_build_grad", i32, [vp, i32, i32, i32, i32, i32, i32, vp, C.POINTER(vp)])
+_sig("vt_gradients", i32, [vp, i32, vp])
+_sig("vt_pyramid_level", i32, [vp, i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)])
+_sig("vt_pyramid_grad", i32, [vp, i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(i32)])
+_sig("vt_pyramid_info", i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t)])
+_sig("vt_pyramid_free", None, [vp])
+_sig("vt_klt_track", i32, [vp, vp, vp, i32, vp, i32, i32, i32, f32, vp, vp, vp, vp])
+_sig("vt_klt_track_ex", i32, [vp, vp, vp, i32, vp, C.POINTER(vt_klt_params), vp, vp, vp,
+                              C.POINTER(vt_klt_diag), vp])
+_sig("vt_klt_track_fb", i32, [vp, vp, vp, i32, C.POINTER(vt_klt_params), vp, vp, vp, C.POINTER(vt_klt_diag), vp])
+_sig("vt_fb_check", i32, [vp, vp, vp, vp, i32, f32, vp, vp])
+_sig("vt_status_str", C.c_char_p, [i32])
+_sig("vt_version", C.c_char_p, [])
+
+
+def header_functions() -> list:
+    """Names of every function declared in include/vt.h."""
+    with open(os.path.join(_build.INCLUDE, "vt.h")) as f:
+        text = f.read()
+    return re.findall(r"^VT_API\s+[\w\s\*]*?\b(vt_\w+)\s*\(", text, flags=re.M)
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(code, what):
+    if code != VT_OK:
+        raise VTError(what, code)
+
+
+def vt_status_str(code: int) -> str:
+    return _lib.vt_status_str(code).decode()
+
+
+def vt_version() -> str:
+    return _lib.vt_version().decode()
+
+
+class Pyramid:
+    """Owning handle of a library pyramid (vt_pyramid*)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+    def free(self):
+        if self.handle:
+            _lib.vt_pyramid_free(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def info(self):
+        return vt_pyramid_info(self)
+
+    def level(self, lvl: int):
+        """Zero-copy torch view (uint8 [h, w], row stride = pitch) of level lvl."""
+        ptr, w, h, pitch = vt_pyramid_level(self, lvl)
+        return _device_view(ptr, (h, w), (pitch, 1), "|u1")
+
+    def grad(self, lvl: int):
+        """Zero-copy view of level lvl's gradient pairs: int16 [h, w, 2] for
+        S16, float16 [h, w, 2] for F16."""
+        ptr, gpitch, t = vt_pyramid_grad(self, lvl)
+        _, w, h, _ = vt_pyramid_level(self, lvl)
+        typestr = "<i2" if t == VT_GRAD_S16 else "<f2"
+        if t == VT_GRAD_NONE:
+            raise ValueError("pyramid has no gradients")
+        return _device_view(ptr, (h, w, 2), (gpitch * 4, 4, 2), typestr)
+
+
+class _CAI:
+    def __init__(self, ptr, shape, strides, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "strides": strides, "typestr": typestr,
+                                         "data": (ptr, False), "version": 3}
+
+
+def _device_view(ptr, shape, strides, typestr):
+    import torch
+
+    return torch.as_tensor(_CAI(ptr, shape, strides, typestr), device="cuda")
+
+
+def _img_args(img):
+    """(pointer, w, h, pitch, on_device) of a 2-D uint8 image."""
+    if hasattr(img, "data_ptr"):  # torch
+        if img.dtype.itemsize != 1 or img.dim() != 2 or img.stride(1) != 1:
+            raise ValueError("image must be a 2-D uint8 tensor with unit column stride")
+        return img.data_ptr(), img.shape[1], img.shape[0], img.stride(0), int(img.is_cuda)
+    import numpy as np
+
+    a = img
+    if a.dtype != np.uint8 or a.ndim != 2 or a.strides[1] != 1:
+        raise ValueError("image must be a 2-D uint8 array with unit column stride")
+    return a.ctypes.data, a.shape[1], a.shape[0], a.strides[0], 0
+
+
+def vt_pyramid_build(img, levels: int, stream=None, out: Pyramid | None = None) -> Pyramid:
+    p, w, h, pitch, dev = _img_args(img)
+    hd = C.c_void_p(out.handle if out is not None else None)
+    _check(_lib.vt_pyramid_build(p, w, h, pitch, levels, dev, _stream(stream), C.byref(hd)), "vt_pyramid_build")
+    return out if out is not None else Pyramid(hd.value)
+
+
+def vt_pyramid_build_grad(img, levels: int, grad_type: int = VT_GRAD_S16, stream=None,
+                          out: Pyramid | None = None) -> Pyramid:
+    p, w, h, pitch, dev = _img_args(img)
+    hd = C.c_void_p(out.handle if out is not None else None)
+    _check(_lib.vt_pyramid_build_grad(p, w, h, pitch, levels, dev, grad_type, _stream(stream), C.byref(hd)),
+           "vt_pyramid_build_grad")
+    return out if out is not None else Pyramid(hd.value)
+
+
+def vt_gradients(pyr: Pyramid, grad_type: int = VT_GRAD_S16, stream=None) -> None:
+    _check(_lib.vt_gradients(pyr, grad_type, _stream(stream)), "vt_gradients")
+
+
+def vt_pyramid_level(pyr: Pyramid, lvl: int):
+    ptr, w, h, pitch = vp(), i32(), i32(), i32()
+    _check(_lib.vt_pyramid_level(pyr, lvl, C.byref(ptr), C.byref(w), C.byref(h), C.byref(pitch)),
+           "vt_pyramid_level")
+    return ptr.value, w.value, h.value, pitch.value
+
+
+def vt_pyramid_grad(pyr: Pyramid, lvl: int):
+    ptr, gp, t = vp(), i32(), i32()
+    _check(_lib.vt_pyramid_grad(pyr, lvl, C.byref(ptr), C.byref(gp), C.byref(t)), "vt_pyramid_grad")
+    return ptr.value, gp.value, t.value
+
+
+def vt_pyramid_info(pyr: Pyramid):
+    w, h, L, b = i32(), i32(), i32(), C.c_size_t()
+    _check(_lib.vt_pyramid_info(pyr, C.byref(w), C.byref(h), C.byref(L), C.byref(b)), "vt_pyramid_info")
+    return w.value, h.value, L.value, b.value
+
+
+def vt_pyramid_free(pyr: Pyramid) -> None:
+    pyr.free()
+
+
+@dataclass
+class KltParams:
+    win: int = 21
+    levels: int = 4
+    max_iters: int = 30
+    eps: float = 0.01
+    min_eig: float = VT_DEFAULT_MIN_EIG
+    fb_thr: float = 0.5
+
+    def c(self) -> vt_klt_params:
+        return vt_klt_params(self.win, self.levels, self.max_iters, self.eps, self.min_eig, self.fb_thr)
+
+
+def _diag(reason=None, iters=None, lmin=None):
+    if reason is None and iters is None and lmin is None:
+        return None
+    return C.byref(vt_klt_diag(_ptr(reason), _ptr(iters), _ptr(lmin)))
+
+
+def vt_klt_track(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None, pts_guess=None, win=21,
+                 levels=4, max_iters=30, eps=0.01, stream=None) -> None:
+    n = int(pts_in.shape[0])
+    _check(_lib.vt_klt_track(prev, cur, _ptr(pts_in), n, _ptr(pts_guess), win, levels, max_iters, eps,
+                             _ptr(pts_out), _ptr(status), _ptr(err), _stream(stream)), "vt_klt_track")
+
+
+def vt_klt_track_ex(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
+                    pts_guess=None, reason=None, iters=None, lmin=None, stream=None) -> None:
+    n = int(pts_in.shape[0])
+    prm = params.c()
+    _check(_lib.vt_klt_track_ex(prev, cur, _ptr(pts_in), n, _ptr(pts_guess), C.byref(prm), _ptr(pts_out),
+                                _ptr(status), _ptr(err), _diag(reason, iters, lmin), _stream(stream)),
+           "vt_klt_track_ex")
+
+
+def vt_klt_track_fb(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
+                    reason=None, iters=None, lmin=None, stream=None) -> None:
+    n = int(pts_in.shape[0])
+    prm = params.c()
+    _check(_lib.vt_klt_track_fb(prev, cur, _ptr(pts_in), n, C.byref(prm), _ptr(pts_out), _ptr(status),
+                                _ptr(err), _diag(reason, iters, lmin), _stream(stream)), "vt_klt_track_fb")
+
+
+def vt_fb_check(p0, p0_back, st_f, st_b, thr, status_out, stream=None) -> None:
+    n = int(p0.shape[0])
+    _check(_lib.vt_fb_check(_ptr(p0), _ptr(p0_back), _ptr(st_f), _ptr(st_b), n, thr, _ptr(status_out),
+                            _stream(stream)), "vt_fb_check")

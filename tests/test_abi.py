@@ -1,0 +1,73 @@
+"""The C-ABI library loads and exports every function include/vt.h declares
+(no GPU needed: nothing here launches a kernel)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_names():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                names += re.findall(r"^VT_API\s+[\w\s\*]*?\b(vt_\w+)\s*\(", f.read(), flags=re.M)
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = set(_header_names())
+    for required in ("vt_pyramid_build", "vt_gradients", "vt_klt_track", "vt_fb_check", "vt_pyramid_level",
+                     "vt_pyramid_free", "vt_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2607_01757_gb300 as vt
+
+    lib = C.CDLL(vt.LIB_PATH)
+    missing = [n for n in _header_names() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(vt.header_functions()) == set(_header_names())
+
+
+def test_status_strings_and_version():
+    import paper_2607_01757_gb300 as vt
+
+    assert vt.vt_status_str(vt.VT_OK) == "VT_OK"
+    assert "invalid argument" in vt.vt_status_str(vt.VT_ERR_ARG)
+    assert "sm_103a" in vt.vt_version()
+
+
+def test_argument_errors_need_no_device():
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import paper_2607_01757_gb300 as vt
+
+    lib = C.CDLL(vt.LIB_PATH)
+    lib.vt_klt_track.restype = C.c_int
+    lib.vt_pyramid_build.restype = C.c_int
+    out = C.c_void_p()
+    # w = 0, null image, too many levels
+    assert lib.vt_pyramid_build(C.c_void_p(1), 0, 10, 10, 1, 0, None, C.byref(out)) == vt.VT_ERR_ARG
+    assert lib.vt_pyramid_build(None, 10, 10, 10, 1, 0, None, C.byref(out)) == vt.VT_ERR_ARG
+    assert lib.vt_pyramid_build(C.c_void_p(1), 10, 10, 10, 9, 0, None, C.byref(out)) == vt.VT_ERR_ARG
+    assert lib.vt_pyramid_build(C.c_void_p(1), 10, 10, 5, 1, 0, None, C.byref(out)) == vt.VT_ERR_ARG
+    # null pyramids
+    assert lib.vt_klt_track(None, None, None, 0, None, 21, 4, 30, C.c_float(0.01), None, None, None, None) \
+        == vt.VT_ERR_ARG
+    lib.vt_fb_check.restype = C.c_int
+    assert lib.vt_fb_check(None, None, None, None, -1, C.c_float(0.5), None, None) == vt.VT_ERR_ARG
+
+
+@pytest.mark.parametrize("win", [9, 15, 21, 31])
+def test_supported_windows_match_header(win):
+    import paper_2607_01757_gb300 as vt
+
+    with open(os.path.join(ROOT, "include", "vt.h")) as f:
+        m = re.search(r"#define VT_SUPPORTED_WINDOWS \{([^}]*)\}", f.read())
+    assert win in [int(t) for t in m.group(1).split(",")]
+    assert win in vt.SUPPORTED_WINDOWS

@@ -1,0 +1,214 @@
+"""Pyramidal LK (K3) and forward-backward check (K4) through the C ABI,
+compared with the FP64 oracle point by point on the same seeded inputs."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import compare, oracle_margin
+
+pytestmark = pytest.mark.gpu
+
+
+def _vt():
+    import paper_2607_01757_gb300 as vt
+
+    return vt
+
+
+def _gpu_track(I, J, pts, prm, fb=False, guess=None, grad=1, stream=None):
+    import torch
+
+    vt = _vt()
+    pI = vt.vt_pyramid_build_grad(I, prm.levels, grad)
+    pJ = vt.vt_pyramid_build_grad(J, prm.levels, grad)
+    n = len(pts)
+    d_in = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).cuda()
+    d_g = None if guess is None else torch.from_numpy(np.ascontiguousarray(guess, np.float32)).cuda()
+    out = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    err = torch.zeros(n, dtype=torch.float32, device="cuda")
+    rs = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    it = torch.zeros(n, dtype=torch.int32, device="cuda")
+    lm = torch.zeros(n, dtype=torch.float32, device="cuda")
+    if fb:
+        vt.vt_klt_track_fb(pI, pJ, d_in, prm, out, st, err, reason=rs, iters=it, lmin=lm)
+    else:
+        vt.vt_klt_track_ex(pI, pJ, d_in, prm, out, st, err, pts_guess=d_g, reason=rs, iters=it, lmin=lm)
+    torch.cuda.synchronize()
+    res = dict(pts=out.cpu().numpy(), status=st.cpu().numpy(), err=err.cpu().numpy(), reason=rs.cpu().numpy(),
+               iters=it.cpu().numpy(), lmin=lm.cpu().numpy())
+    pI.free()
+    pJ.free()
+    return res
+
+
+def _ref(I, J, pts, prm, fb=False, guess=None):
+    pI, pJ = oracle.build_pyramid(I, prm.levels), oracle.build_pyramid(J, prm.levels)
+    if fb:
+        return oracle.track_fb(pI, pJ, pts, prm.win, prm.levels, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
+    return oracle.track(pI, pJ, pts, prm.win, prm.levels, prm.max_iters, prm.eps, prm.min_eig, guess=guess)
+
+
+def _check(g, r, label, fb=False):
+    pts_ref = r.fwd.pts if fb else r.pts
+    st = compare(g["pts"], g["status"], pts_ref, r.status, oracle_margin(r), label)
+    both = (g["status"] == 1) & (r.status == 1)
+    err_ref = r.fwd.err if fb else r.err
+    np.testing.assert_allclose(g["err"][both], err_ref[both], rtol=2e-3, atol=2e-3)
+    return st
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return synth.make_config1(1)
+
+
+def test_config1_forward(cfg1):
+    vt = _vt()
+    prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
+    g = _gpu_track(cfg1.I, cfg1.J, cfg1.pts, prm)
+    r = _ref(cfg1.I, cfg1.J, cfg1.pts, prm)
+    st = _check(g, r, "config1 forward")
+    assert st["tracked_ref"] >= 140
+    agree = (g["status"] == 1) & (r.status == 1) & (r.margin.min(axis=1) > 1e-3)
+    # iteration counts agree wherever no convergence decision was marginal
+    assert (g["iters"][agree] == r.iters[agree]).mean() > 0.98
+    np.testing.assert_allclose(g["lmin"][agree], r.lmin[agree], rtol=1e-4)
+
+
+def test_config1_forward_backward(cfg1):
+    vt = _vt()
+    prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
+    g = _gpu_track(cfg1.I, cfg1.J, cfg1.pts, prm, fb=True)
+    r = _ref(cfg1.I, cfg1.J, cfg1.pts, prm, fb=True)
+    _check(g, r, "config1 fb", fb=True)
+    same = g["status"] == r.status
+    assert np.all(g["reason"][same & (r.status == 0)] == r.reason[same & (r.status == 0)])
+
+
+def test_fused_fb_equals_separate_calls(cfg1):
+    """vt_klt_track_fb == vt_klt_track_ex forward, _ex backward, vt_fb_check."""
+    import torch
+
+    vt = _vt()
+    prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
+    pI = vt.vt_pyramid_build_grad(cfg1.I, 4)
+    pJ = vt.vt_pyramid_build_grad(cfg1.J, 4)
+    n = len(cfg1.pts)
+    p0 = torch.from_numpy(cfg1.pts).cuda()
+    f_out, b_out = torch.zeros_like(p0), torch.zeros_like(p0)
+    f_st, b_st, fb_st = (torch.zeros(n, dtype=torch.uint8, device="cuda") for _ in range(3))
+    vt.vt_klt_track_ex(pI, pJ, p0, prm, f_out, f_st)
+    vt.vt_klt_track_ex(pJ, pI, f_out, prm, b_out, b_st)
+    vt.vt_fb_check(p0, b_out, f_st, b_st, prm.fb_thr, fb_st)
+    u_out, u_st = torch.zeros_like(p0), torch.zeros(n, dtype=torch.uint8, device="cuda")
+    vt.vt_klt_track_fb(pI, pJ, p0, prm, u_out, u_st)
+    torch.cuda.synchronize()
+    assert torch.equal(u_st, fb_st)
+    ok = u_st.bool()
+    assert (u_out[ok] - f_out[ok]).abs().max().item() <= 1e-5
+
+
+@pytest.mark.parametrize("win", [9, 15, 31])
+def test_other_windows(cfg1, win):
+    vt = _vt()
+    prm = vt.KltParams(win=win, levels=4, max_iters=30, eps=0.01, fb_thr=0.5,
+                       min_eig=1e-4 if win >= 15 else 5e-5)
+    g = _gpu_track(cfg1.I, cfg1.J, cfg1.pts[:97], prm, fb=True)
+    r = _ref(cfg1.I, cfg1.J, cfg1.pts[:97], prm, fb=True)
+    _check(g, r, f"win {win}", fb=True)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 5, 37])
+def test_ragged_point_counts(cfg1, n):
+    vt = _vt()
+    prm = vt.KltParams()
+    pts = cfg1.pts[:n]
+    if n == 0:
+        import torch
+
+        pI = vt.vt_pyramid_build_grad(cfg1.I, 4)
+        e = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
+        s = torch.zeros(0, dtype=torch.uint8, device="cuda")
+        vt.vt_klt_track_ex(pI, pI, e, prm, e, s)
+        vt.vt_klt_track_fb(pI, pI, e, prm, e, s)
+        return
+    g = _gpu_track(cfg1.I, cfg1.J, pts, prm)
+    r = _ref(cfg1.I, cfg1.J, pts, prm)
+    _check(g, r, f"n={n}")
+
+
+def test_zero_motion_and_degenerate_points(cfg1):
+    vt = _vt()
+    prm = vt.KltParams()
+    w, h = cfg1.I.shape[1], cfg1.I.shape[0]
+    pts = np.concatenate([cfg1.pts[:20], np.array([[0.0, 0.0], [w - 1.0, h - 1.0], [-0.5, 10.0], [w + 3.0, 5.0],
+                                                   [np.nan, 3.0], [5.0, 5.0], [w - 2.0, 100.0]], np.float32)])
+    g = _gpu_track(cfg1.I, cfg1.I, pts, prm)
+    r = _ref(cfg1.I, cfg1.I, pts, prm)
+    _check(g, r, "zero motion / border points")
+    ok = r.status == 1
+    assert np.array_equal(g["pts"][ok], pts[ok])  # I == J: flow is exactly zero
+    assert np.all(g["reason"][[22, 23, 24]] == vt.VT_LOST_INPUT)
+    # flat image: every point is rejected by the eigenvalue test
+    flat = np.full_like(cfg1.I, 77)
+    g = _gpu_track(flat, flat, cfg1.pts[:8], prm)
+    assert np.all(g["status"] == 0) and np.all(g["reason"] == vt.VT_LOST_EIG)
+
+
+def test_guess_and_iteration_cap(cfg1):
+    vt = _vt()
+    prm = vt.KltParams(max_iters=1, eps=0.0)
+    g = _gpu_track(cfg1.I, cfg1.J, cfg1.pts, prm, guess=cfg1.gt.astype(np.float32))
+    r = _ref(cfg1.I, cfg1.J, cfg1.pts, prm, guess=cfg1.gt)
+    _check(g, r, "guess + max_iters=1")
+    assert np.all(g["iters"][g["status"] == 1] == 4)
+    far = cfg1.pts[:5] + np.array([3000.0, 0.0], np.float32)
+    g = _gpu_track(cfg1.I, cfg1.J, cfg1.pts[:5], vt.KltParams(), guess=far)
+    assert np.all(g["status"] == 0) and np.all(g["reason"] == vt.VT_LOST_OOB)
+
+
+def test_deterministic_repeat(cfg1):
+    vt = _vt()
+    prm = vt.KltParams()
+    a = _gpu_track(cfg1.I, cfg1.J, cfg1.pts, prm, fb=True)
+    b = _gpu_track(cfg1.I, cfg1.J, cfg1.pts, prm, fb=True)
+    for k in ("pts", "status", "err", "iters"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_fb_check_kernel():
+    import torch
+
+    vt = _vt()
+    p0 = torch.tensor([[10.0, 10.0], [10.0, 10.0], [10.0, 10.0], [1.0, 1.0]], device="cuda")
+    p1 = torch.tensor([[10.5, 10.0], [10.0, 10.5000005], [10.25, 10.25], [1.0, 1.0]], device="cuda")
+    sf = torch.tensor([1, 1, 1, 0], dtype=torch.uint8, device="cuda")
+    sb = torch.ones(4, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    vt.vt_fb_check(p0, p1, sf, sb, 0.5, out)
+    torch.cuda.synchronize()
+    ref, _, _ = oracle.fb_check(p0.cpu().numpy(), p1.cpu().numpy(), sf.cpu().numpy(), sb.cpu().numpy(), 0.5)
+    assert out.cpu().numpy().tolist() == ref.tolist() == [1, 0, 1, 0]
+
+
+def test_argument_errors():
+    import torch
+
+    vt = _vt()
+    img = np.zeros((64, 64), np.uint8)
+    p = vt.vt_pyramid_build(img, 3)
+    e = torch.zeros((4, 2), device="cuda")
+    s = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(vt.VTError):  # no gradients yet
+        vt.vt_klt_track_ex(p, p, e, vt.KltParams(levels=3), e, s)
+    vt.vt_gradients(p)
+    for bad in (vt.KltParams(levels=4), vt.KltParams(levels=3, win=20), vt.KltParams(levels=3, win=11),
+                vt.KltParams(levels=3, max_iters=0), vt.KltParams(levels=3, eps=-1.0)):
+        with pytest.raises(vt.VTError):
+            vt.vt_klt_track_ex(p, p, e, bad, e, s)
+    q = vt.vt_pyramid_build_grad(img, 3, vt.VT_GRAD_F16)
+    with pytest.raises(vt.VTError):  # fused FB needs one gradient type
+        vt.vt_klt_track_fb(p, q, e, vt.KltParams(levels=3), e, s)

@@ -1,0 +1,108 @@
+"""Pyramid (K1) and Scharr gradients (K2): bit-exact against the oracle,
+through the C ABI, on tiny, ragged and full-size images."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1, 1), (2, 3), (5, 1), (1, 7), (7, 7), (8, 8), (17, 33), (63, 65), (129, 47), (200, 131), (752, 480),
+         (640, 480), (1280, 1024), (1920, 1200)]
+
+
+def _img(w, h, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if w * h < 4096:
+        return rng.integers(0, 256, (h, w), dtype=np.uint8)
+    tex = synth.BlobTexture(seed, extent=(-50, -50, w + 50, h + 50), n_blobs=max(20, int(400 * w * h / 361000)),
+                            blob_radius_sigmas=4.0)
+    img = synth.texture.quantize_u8(tex.eval_affine(w, h, np.array([[1.0, 0, 0], [0, 1.0, 0]])))
+    # salt a few extreme pixels so saturating values are exercised
+    idx = rng.integers(0, w * h, 64)
+    img.reshape(-1)[idx[:32]] = 0
+    img.reshape(-1)[idx[32:]] = 255
+    return img
+
+
+def _levels_for(w, h):
+    return max(1, min(6, int(np.log2(max(1, min(w, h)))) + 2))
+
+
+@pytest.mark.parametrize("w,h", SIZES)
+def test_pyramid_and_gradients_bit_exact(w, h):
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    img = _img(w, h, seed=w * 1000 + h)
+    L = _levels_for(w, h)
+    ref = oracle.build_pyramid(img, L)
+    # device input, separate gradient pass
+    dimg = torch.from_numpy(img).cuda()
+    p = vt.vt_pyramid_build(dimg, L)
+    vt.vt_gradients(p, vt.VT_GRAD_S16)
+    # host input, fused pyramid + gradients
+    q = vt.vt_pyramid_build_grad(img, L, vt.VT_GRAD_S16)
+    torch.cuda.synchronize()
+    for l in range(L):
+        for pyr in (p, q):
+            lv = pyr.level(l).cpu().numpy()
+            assert lv.shape == ref.levels[l].shape
+            assert np.array_equal(lv, ref.levels[l]), (w, h, l)
+            g = pyr.grad(l).cpu().numpy()
+            assert np.array_equal(g[..., 0], ref.gx[l]), (w, h, l)
+            assert np.array_equal(g[..., 1], ref.gy[l]), (w, h, l)
+    p.free()
+    q.free()
+
+
+@pytest.mark.parametrize("w,h", [(7, 5), (752, 480), (1280, 1024)])
+def test_f16_gradients_round_to_nearest_even(w, h):
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    img = _img(w, h, seed=7 * w + h)
+    L = _levels_for(w, h)
+    ref = oracle.build_pyramid(img, L)
+    p = vt.vt_pyramid_build_grad(img, L, vt.VT_GRAD_F16)
+    q = vt.vt_pyramid_build(img, L)
+    vt.vt_gradients(q, vt.VT_GRAD_F16)
+    torch.cuda.synchronize()
+    for l in range(L):
+        # numpy's float64 -> float16 conversion rounds to nearest even
+        ex = (ref.gx[l] / 32.0).astype(np.float16)
+        ey = (ref.gy[l] / 32.0).astype(np.float16)
+        for pyr in (p, q):
+            g = pyr.grad(l).cpu().numpy()
+            assert np.array_equal(g[..., 0].view(np.uint16), ex.view(np.uint16))
+            assert np.array_equal(g[..., 1].view(np.uint16), ey.view(np.uint16))
+
+
+def test_rebuild_in_place_and_pitch():
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    a = _img(300, 200, 1)
+    b = _img(300, 200, 2)
+    p = vt.vt_pyramid_build_grad(a, 4, vt.VT_GRAD_S16)
+    h0 = p.handle
+    # a strided device view of a wider buffer as input (pitch > width)
+    big = torch.zeros((200, 320), dtype=torch.uint8, device="cuda")
+    big[:, :300] = torch.from_numpy(b).cuda()
+    vt.vt_pyramid_build_grad(big[:, :300], 4, vt.VT_GRAD_S16, out=p)
+    torch.cuda.synchronize()
+    assert p.handle == h0
+    ref = oracle.build_pyramid(b, 4)
+    for l in range(4):
+        assert np.array_equal(p.level(l).cpu().numpy(), ref.levels[l])
+        assert np.array_equal(p.grad(l).cpu().numpy()[..., 0], ref.gx[l])
+    # a mismatched shape is refused
+    with pytest.raises(vt.VTError):
+        vt.vt_pyramid_build_grad(_img(301, 200, 3), 4, vt.VT_GRAD_S16, out=p)
+    w, h, L, nbytes = p.info()
+    assert (w, h, L) == (300, 200, 4) and nbytes > 0
