@@ -1,0 +1,567 @@
+#!/usr/bin/env python
+"""Tracked features/s and p99 frame latency of pyramidal LK tracking on GB300:
+batched (persistent launches, CUDA graph) vs plain (single-pair calls per stream).
+
+Default workload (one GPU): 32 independent camera streams of uneven shapes
+(640x480 .. 1920x1200), mono or stereo, 200-2000 keypoints, 4-6 pyramid
+levels, window 21, 30 iterations, eps 0.01 px, FB threshold 0.5 px.  One step
+takes a new frame on every stream: pyramid + gradients of the new frame(s),
+prev->cur tracking with forward-backward check, and for stereo streams the
+left->right tracking with forward-backward check.  A tracked feature is one
+keypoint taken through its stream's step (counted whether or not it survives).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+streams (replicas, no data exchange); timings are max-reduced.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tracked features/s & p99 frame latency, batched/served vs plain KLT, 1 GB300"
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--streams", type=int, default=32)
+    ap.add_argument("--frames", type=int, default=4, help="distinct frames per stream (ping-pong sequence)")
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true", help="4 streams, for profiler captures")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def pingpong(t, F):
+    if F <= 1:
+        return 0
+    P = 2 * (F - 1)
+    k = t % P
+    return k if k < F else P - k
+
+
+def _render(args):
+    import synth
+
+    spec, F = args
+    return synth.render_stream_frames(spec, F)
+
+
+def make_workload(n_streams, F, seed, procs):
+    """Stream specs and their frames (rendered in a spawn pool: no CUDA yet)."""
+    import multiprocessing as mp
+
+    import synth
+
+    specs = synth.make_stream_mix(n_streams, seed=seed)
+    if procs > 1 and n_streams > 1:
+        with mp.get_context("spawn").Pool(min(procs, n_streams)) as pool:
+            frames = pool.map(_render, [(sp, F) for sp in specs])
+    else:
+        frames = [_render((sp, F)) for sp in specs]
+    return specs, frames
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.uuid], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - clocks are reported as unavailable
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 7:
+                    continue
+                try:
+                    sm.append(float(p[0]))
+                    mx.append(float(p[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- native arm
+def run_native(a, rank, world, local_rank):
+    import numpy as np
+
+    specs, frames = make_workload(a.streams, a.frames, a.seed + 1000 * rank, os.cpu_count() or 1)
+
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.engine import BatchedTracker
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+    F = a.frames
+    prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
+    tr = BatchedTracker(specs, prm)
+    S = len(specs)
+    sids = list(range(S))
+    # device frame store: frames and keypoints of every stream
+    left = [[torch.from_numpy(fr.left[k]).to(dev) for k in range(F)] for fr in frames]
+    right = [[torch.from_numpy(fr.right[k]).to(dev) if fr.right[k] is not None else None for k in range(F)]
+             for fr in frames]
+    kps = [[torch.from_numpy(fr.kps[k]).to(dev) for k in range(F)] for fr in frames]
+    nkp = [[int(fr.kps[k].shape[0]) for k in range(F)] for fr in frames]
+
+    def step_args(t):
+        fp, fc = pingpong(t - 1, F), pingpong(t, F)
+        L = [left[i][fc] for i in sids]
+        R = [right[i][fc] for i in sids]
+        kt = [kps[i][fp] for i in sids]
+        ks = [kps[i][fc] for i in sids]
+        n_t = [nkp[i][fp] if t > 0 else 0 for i in sids]
+        n_s = [nkp[i][fc] for i in sids]
+        return L, R, kt, ks, n_t, n_s
+
+    features = lambda t: sum(step_args(t)[4])  # noqa: E731
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def batched_prepare(t, flops=None):
+        # host-only: job tables of step t into the pinned staging buffer
+        L, R, kt, ks, n_t, n_s = step_args(t)
+        tr.stage(tr.step_tables(sids, n_t, n_s, L, R, flops=flops, kpt=kt, kps=ks))
+
+    def batched_launch(t, events=None, graph=True):
+        tr.run(stream, graph=graph, events=events)
+        tr.advance(sids)
+
+    def batched_step(t, events=None, graph=True, flops=None):
+        batched_prepare(t, flops)
+        batched_launch(t, events, graph)
+
+    def plain_step(t):
+        L, R, kt, ks, n_t, n_s = step_args(t)
+        tr.plain_step(sids, n_t, n_s, L, R, stream, kpt=kt, kps=ks)
+        tr.advance(sids)
+
+    def timed(fn, t0, K, prepare=None, flush_between=True):
+        """Per-step device time (CUDA events on the launching stream).  The
+        L2 flush and the host-only preparation of step i sit outside its events."""
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        feats = 0
+        for i in range(K):
+            if flush_between:
+                flush.fill_(i & 0xFF)
+            if prepare is not None:
+                prepare(t0 + i)
+            starts[i].record(stream)
+            fn(t0 + i)
+            ends[i].record(stream)
+            feats += features(t0 + i)
+        torch.cuda.synchronize()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return ms, feats
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        return float(tt.item())
+
+    # ---------------- batched (headline) ----------------
+    uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clk = ClockSampler(uuid)
+    t = 0
+    batched_step(t)  # frame 0: pyramids only (no previous frame yet)
+    t += 1
+    for _ in range(a.warmup):
+        batched_step(t)
+        t += 1
+    barrier()
+    # clocks are sampled every 100 ms from here through the timed region and
+    # the per-kernel timing pass (the timed region alone is tens of ms)
+    clk.start()
+    time.sleep(0.25)
+    ms, feats = timed(batched_launch, t, a.steps, prepare=batched_prepare)
+    barrier()
+    t += a.steps
+    total_ms = max_over_ranks(sum(ms))
+    feats_all = sum_over_ranks(feats)
+    value = feats_all / (total_ms / 1e3)
+    info = vt.vt_batch_info(tr.batch)
+    launches_per_step = info["launches_per_run"]
+
+    # ---------------- live per-kernel timing (direct launches, same steps) -------
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)  # torch creates the CUDA event on first record
+        return e
+
+    klt_ms, pyr_ms = [], []
+    for i in range(a.steps):
+        flush.fill_(i & 0xFF)
+        e = [ev(), ev(), ev(), ev()]
+        batched_step(t, events=e)
+        t += 1
+        torch.cuda.synchronize()
+        pyr_ms.append(e[0].elapsed_time(e[1]))
+        klt_ms.append(e[2].elapsed_time(e[3]))
+    # algorithmic FLOPs of the tracking launch, per distinct step of the period
+    P = max(1, 2 * (F - 1))
+    flops_per_step = []
+    for j in range(P):
+        fl = [(torch.zeros(max(1, s.n_max), dtype=torch.int32, device=dev),
+               torch.zeros(max(1, s.n_max), dtype=torch.int32, device=dev)) for s in tr.streams]
+        batched_step(t, graph=False, flops=fl)
+        _, _, _, _, n_t, n_s = step_args(t)
+        torch.cuda.synchronize()
+        tot = 0
+        for k, s in enumerate(tr.streams):
+            tot += int(fl[k][0][:n_t[k]].sum().item())
+            if s.stereo:
+                tot += int(fl[k][1][:n_s[k]].sum().item())
+        flops_per_step.append(tot)
+        t += 1
+    # keep the GPU busy on the timed work for a few hundred ms more so the
+    # clock samples see it under load
+    w0 = time.perf_counter()
+    while time.perf_counter() - w0 < 0.6:
+        batched_step(t)
+        t += 1
+        torch.cuda.synchronize()
+    clocks = clk.stop()
+    klt_flops = statistics.mean(flops_per_step)
+    klt_avg_s = statistics.mean(klt_ms) / 1e3
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = klt_flops / klt_avg_s / 1e12
+    # pyramid algorithmic bytes (fused build): per level l of a frame, read
+    # level l (the caller image for l = 0), write level l+1, write 4 B/px of
+    # gradients, and for l = 0 write the level-0 copy
+    pyr_bytes = 0
+    for s in tr.streams:
+        w, h = s.w, s.h
+        dims = []
+        for _ in range(s.levels):
+            dims.append((w, h))
+            w, h = (w + 1) // 2, (h + 1) // 2
+        b = dims[0][0] * dims[0][1]  # level-0 copy
+        for l, (lw, lh) in enumerate(dims):
+            b += lw * lh + 4 * lw * lh
+            if l + 1 < len(dims):
+                b += dims[l + 1][0] * dims[l + 1][1]
+        pyr_bytes += b * (2 if s.stereo else 1)
+    pyr_avg_s = statistics.mean(pyr_ms) / 1e3
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # ---------------- plain path ----------------
+    plain = None
+    if not a.no_plain:
+        for _ in range(max(1, a.warmup // 2)):
+            plain_step(t)
+            t += 1
+        barrier()
+        pms, pfeats = timed(plain_step, t, a.steps)
+        barrier()
+        t += a.steps
+        ptot = max_over_ranks(sum(pms))
+        L_, R_, kt_, ks_, n_t_, n_s_ = step_args(t)
+        plain = {"value": sum_over_ranks(pfeats) / (ptot / 1e3), "ms_per_step": ptot / a.steps,
+                 "p50_ms": float(np.percentile(pms, 50)), "p99_ms": float(np.percentile(pms, 99)),
+                 "gpu_launches_per_step": tr.plain_launches(sids, n_t_, n_s_)}
+
+    # ---------------- end to end: host frames in, host results out ----------------
+    e2e = None
+    if not a.no_e2e:
+        pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
+        hleft = [[pin(fr.left[k]) for k in range(F)] for fr in frames]
+        hright = [[pin(fr.right[k]) if fr.right[k] is not None else None for k in range(F)] for fr in frames]
+        hkps = [[pin(fr.kps[k]) for k in range(F)] for fr in frames]
+        hout = [(torch.empty((s.n_max, 2), dtype=torch.float32).pin_memory(),
+                 torch.empty(s.n_max, dtype=torch.uint8).pin_memory(),
+                 torch.empty((s.n_max, 2), dtype=torch.float32).pin_memory(),
+                 torch.empty(s.n_max, dtype=torch.uint8).pin_memory()) for s in tr.streams]
+        h2d = {"b": 0}
+        d2h = {"b": 0}
+
+        def e2e_step(t_):
+            fp, fc = pingpong(t_ - 1, F), pingpong(t_, F)
+            n_t = [nkp[i][fp] for i in sids]
+            n_s = [nkp[i][fc] for i in sids]
+            for i, s in enumerate(tr.streams):
+                s.in_left.copy_(hleft[i][fc], non_blocking=True)
+                h2d["b"] += s.w * s.h
+                s.kp_t[:n_t[i]].copy_(hkps[i][fp], non_blocking=True)
+                h2d["b"] += 8 * n_t[i]
+                if s.stereo:
+                    s.in_right.copy_(hright[i][fc], non_blocking=True)
+                    s.kp_s[:n_s[i]].copy_(hkps[i][fc], non_blocking=True)
+                    h2d["b"] += s.w * s.h + 8 * n_s[i]
+            tr.stage(tr.step_tables(sids, n_t, n_s))
+            tr.run(stream, graph=True)
+            tr.advance(sids)
+            for i, s in enumerate(tr.streams):
+                hout[i][0][:n_t[i]].copy_(s.out_t[0][:n_t[i]], non_blocking=True)
+                hout[i][1][:n_t[i]].copy_(s.out_t[1][:n_t[i]], non_blocking=True)
+                d2h["b"] += 9 * n_t[i]
+                if s.stereo:
+                    hout[i][2][:n_s[i]].copy_(s.out_s[0][:n_s[i]], non_blocking=True)
+                    hout[i][3][:n_s[i]].copy_(s.out_s[1][:n_s[i]], non_blocking=True)
+                    d2h["b"] += 9 * n_s[i]
+
+        for _ in range(a.warmup):
+            e2e_step(t)
+            stream.synchronize()
+            t += 1
+        h2d["b"] = d2h["b"] = 0
+        barrier()
+        ems, efeats = [], 0
+        for i in range(a.steps):
+            w0 = time.perf_counter()
+            e2e_step(t)
+            stream.synchronize()  # results visible on the host
+            ems.append((time.perf_counter() - w0) * 1e3)
+            efeats += features(t)
+            t += 1
+        barrier()
+        etot = max_over_ranks(sum(ems))
+        e2e = {"value": sum_over_ranks(efeats) / (etot / 1e3), "unit": "features/s",
+               "timing": "host wall clock per step: H2D of frames + keypoints, batched run (graph), "
+                         "D2H of points + status, stream synchronised",
+               "h2d_bytes_per_step": h2d["b"] // a.steps, "d2h_bytes_per_step": d2h["b"] // a.steps,
+               "p50_ms": float(np.percentile(ems, 50)), "p99_ms": float(np.percentile(ems, 99))}
+
+    # ---------------- CPU baseline (oracle), rank 0 at N = 1 only -------------
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(specs, frames, prm, a.cpu_seconds)
+
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "features/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "impl": "native",
+        "config": {
+            "workload": f"batched: {S} camera streams (640x480..1920x1200, mono/stereo, 200-2000 keypoints, "
+                        f"4-6 levels), one new frame per stream per step, FB-checked temporal + stereo tracking",
+            "streams": S,
+            "stereo_streams": sum(1 for s in specs if s.stereo),
+            "features_per_step": feats // a.steps,
+            "frames_per_stream": F,
+            "win": prm.win, "levels": "per stream (4-6)", "max_iters": prm.max_iters, "eps": prm.eps,
+            "fb_thr": prm.fb_thr,
+            "l2": "flushed between steps (256 MB write outside the per-step CUDA events)",
+            "graph": True,
+            "seed": a.seed,
+            "parallelism": "replicas" if world > 1 else "single",
+        },
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "max": float(max(ms))},
+        "plain": plain,
+        "speedup_vs_plain": (value / plain["value"]) if plain else None,
+        "e2e": e2e,
+        "gpu_launches": a.steps * launches_per_step,
+        "roofline": {"bound": "alu", "kernel": "k_klt_batch", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "flops_per_launch": klt_flops, "launch_ms": klt_avg_s * 1e3,
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "roofline_pyramid": {"bound": "hbm", "kernel": "k_pyr_batch+k_scharr_batch", "achieved": pyr_bytes / pyr_avg_s
+                             / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": None,
+                             "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    tr.free()
+    if dist is not None:
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+def cpu_baseline(specs, frames, prm, seconds):
+    """The FP64 oracle, single-threaded, on a bounded sample of step 1 of the
+    same workload: pyramids + Scharr of the frames it needs, then the
+    FB-checked tracking of each stream's points, stream after stream, until
+    `seconds` have passed."""
+    import oracle
+
+    t0 = time.perf_counter()
+    feats = 0
+    streams = 0
+    pts_done = 0
+    for sp, fr in zip(specs, frames):
+        L = prm.levels
+        p0 = oracle.build_pyramid(fr.left[0], sp.levels)
+        p1 = oracle.build_pyramid(fr.left[1], sp.levels)
+        chunk = 64
+        kp = fr.kps[0]
+        for c in range(0, len(kp), chunk):
+            oracle.track_fb(p0, p1, kp[c:c + chunk], prm.win, L, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
+            pts_done += len(kp[c:c + chunk])
+            if sp.stereo:
+                if c == 0:
+                    pr = oracle.build_pyramid(fr.right[1], sp.levels)
+                kq = fr.kps[1][c:c + chunk]
+                oracle.track_fb(p1, pr, kq, prm.win, L, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
+            feats += len(kp[c:c + chunk])
+            if time.perf_counter() - t0 > seconds:
+                break
+        streams += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": feats / dt, "unit": "features/s", "cores": 1, "kind": "oracle",
+            "sample": f"step 1 of the same workload: {feats} features of {streams} stream(s) incl. their pyramids, "
+                      f"FP64 single-threaded C, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    """The FP64 oracle as the reference arm: each step tracks a bounded sample
+    (the first 128 keypoints of one stream, cycling over streams) of the same
+    workload on the host cores, pyramids included."""
+    if rank != 0:
+        return None
+    import oracle
+
+    specs, frames = make_workload(min(a.streams, 8), a.frames, a.seed, os.cpu_count() or 1)
+    prm_levels = min(sp.levels for sp in specs)
+    F = a.frames
+
+    def one(t):
+        sp, fr = specs[t % len(specs)], frames[t % len(specs)]
+        fp, fc = pingpong(t, F), pingpong(t + 1, F)
+        p0 = oracle.build_pyramid(fr.left[fp], sp.levels)
+        p1 = oracle.build_pyramid(fr.left[fc], sp.levels)
+        kp = fr.kps[fp][:128]
+        oracle.track_fb(p0, p1, kp, 21, prm_levels, 30, 0.01, 1e-4, 0.5)
+        if sp.stereo:
+            pr = oracle.build_pyramid(fr.right[fc], sp.levels)
+            oracle.track_fb(p1, pr, fr.kps[fc][:128], 21, prm_levels, 30, 0.01, 1e-4, 0.5)
+        return len(kp)
+
+    for i in range(a.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    feats = 0
+    times = []
+    for i in range(a.steps):
+        s0 = time.perf_counter()
+        feats += one(a.warmup + i)
+        times.append(time.perf_counter() - s0)
+    dt = time.perf_counter() - t0
+    v = feats / dt
+    times.sort()
+    return {
+        "metric": METRIC, "value": v, "unit": "features/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "batched stream mix, bounded sample per step: 128 keypoints of one stream "
+                               "(temporal + stereo FB tracking, pyramids included)", "streams": len(specs)},
+        "latency_ms": {"p50": times[len(times) // 2] * 1e3, "p99": times[min(len(times) - 1,
+                                                                              int(0.99 * len(times)))] * 1e3},
+        "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "kind": "oracle",
+                         "sample": "128 keypoints of one stream per step"},
+        "e2e": {"value": v, "unit": "features/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    a = parse()
+    rank, world, local_rank = rank_info()
+    if a.small:
+        a.streams = min(a.streams, 4)
+        a.no_cpu = True
+    if a.impl == "reference":
+        res = run_reference(a, rank, world)
+    else:
+        res = run_native(a, rank, world, local_rank)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

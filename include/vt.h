@@ -115,6 +115,13 @@ VT_API vt_status vt_gradients(vt_pyramid *p, vt_grad_type t, void *cuda_stream);
 VT_API vt_status vt_pyramid_build_grad(const uint8_t *img, int w, int h, int pitch, int levels, int img_on_device,
                                 vt_grad_type t, void *cuda_stream, vt_pyramid **out);
 
+/*
+ * vt_pyramid_create - allocate (one cudaMalloc) an empty pyramid for w x h
+ * images with `levels` levels, for use as a vt_batch build target.  Same
+ * argument rules as vt_pyramid_build.  Synchronous.
+ */
+VT_API vt_status vt_pyramid_create(int w, int h, int levels, vt_pyramid **out);
+
 /* Level `lvl` of `p`: device image pointer, size and pitch (bytes). */
 VT_API vt_status vt_pyramid_level(const vt_pyramid *p, int lvl, const uint8_t **ptr, int *w, int *h, int *pitch);
 
@@ -171,8 +178,13 @@ typedef struct vt_klt_params {
 /* Optional per-point diagnostics (device arrays of n entries, each nullable). */
 typedef struct vt_klt_diag {
     uint8_t *reason; /* VT_TRACKED / VT_LOST_* */
-    int32_t *iters;  /* Newton iterations summed over levels (forward pass) */
-    float *lmin;     /* normalised lambda_min of G at the last level examined */
+    int32_t *iters;  /* Newton iterations summed over levels (and over both
+                        passes in the fused forward-backward calls) */
+    float *lmin;     /* normalised lambda_min of G at the last level examined
+                        (forward pass) */
+    int32_t *flops;  /* algorithmic FLOPs spent on the point: win^2 x (27 per
+                        template sweep + 12 per Newton sweep + 9 per error
+                        sweep), both passes in the fused calls */
 } vt_klt_diag;
 
 /* vt_klt_track with an explicit parameter block and diagnostics (diag nullable). */
@@ -199,6 +211,88 @@ VT_API vt_status vt_fb_check(const float *p0, const float *p0_back, const uint8_
 VT_API vt_status vt_klt_track_fb(const vt_pyramid *prev, const vt_pyramid *cur, const float *pts_in, int n,
                           const vt_klt_params *prm, float *pts_out, uint8_t *status, float *err,
                           const vt_klt_diag *diag, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batched tracking: the frames and tracking tasks of many independent camera
+ * streams in one fixed sequence of persistent launches (one per pyramid
+ * level, one for the last levels' gradients, one for every tracking task),
+ * replayable as a CUDA graph.  Results equal those of the single-pair calls
+ * (vt_pyramid_build_grad, vt_klt_track_ex / vt_klt_track_fb) on the same
+ * inputs; a point's result does not depend on the rest of the batch.
+ * ---------------------------------------------------------------------- */
+
+/* Build pyramid `pyr` (levels and gradients) from the device image `img`
+ * (the pyramid's w x h, `pitch` bytes per row, any alignment). */
+typedef struct vt_frame_job {
+    const uint8_t *img;
+    int pitch;
+    vt_pyramid *pyr;
+} vt_frame_job;
+
+/* Track n points (device float2) from `prev` to `cur`; fb = 1 runs the
+ * forward-backward variant (vt_klt_track_fb semantics).  Outputs are device
+ * arrays of n entries; err, reason and flops are nullable.  A pyramid built
+ * in the same run may serve as prev or cur.  levels: pyramid levels used by
+ * this task (0 = the run's vt_klt_params.levels). */
+typedef struct vt_track_task {
+    const vt_pyramid *prev;
+    const vt_pyramid *cur;
+    const float *pts_in;
+    int n;
+    int fb;
+    float *pts_out;
+    uint8_t *status;
+    float *err;
+    uint8_t *reason;
+    int32_t *flops;
+    int levels;
+} vt_track_task;
+
+typedef struct vt_batch vt_batch; /* opaque: pinned + device job tables, work counter, graphs */
+
+/* Capacity: at most max_frames pyramid builds and max_tasks tasks per run.
+ * Allocates two pinned and two device table buffers (a few tens of KB). */
+VT_API vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out);
+
+/* Frees the batch (synchronises the device first; NULL is ignored). */
+VT_API void vt_batch_free(vt_batch *b);
+
+/*
+ * Launch shape of the persistent KLT kernel: warps per CTA (4 or 8) and CTAs
+ * per SM (0 = as many as fit); CTAs of the pyramid launches (0 = SMs x
+ * resident CTAs).  Takes effect at the next vt_batch_set.
+ */
+VT_API vt_status vt_batch_config(vt_batch *b, int klt_warps_per_cta, int klt_ctas_per_sm, int pyr_ctas);
+
+/*
+ * Stage the next run: `nframes` pyramid builds with gradient type `gtype`
+ * (S16 or F16) and `ntasks` tracking tasks with parameters `prm` (the window
+ * and gradient type are per run).  Host-only: copies the descriptors into a
+ * pinned staging buffer (two alternate, so a run may still execute while
+ * the next is staged; staging waits for the run that last used the buffer).
+ * Tasks of one run see the pyramids as they are after this run's builds.
+ */
+VT_API vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_grad_type gtype,
+                              const vt_track_task *tasks, int ntasks, const vt_klt_params *prm);
+
+/* Run the staged batch with direct launches on `cuda_stream`.  Runs of one
+ * batch must be issued on one stream (or otherwise serialised). */
+VT_API vt_status vt_batch_run(vt_batch *b, void *cuda_stream);
+
+/* Same as vt_batch_run through a CUDA graph: captured (on an internal stream)
+ * the first time a staging buffer is run with a given topology (deepest
+ * pyramid, gradient type, window, launch shape), then replayed. */
+VT_API vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream);
+
+/* vt_batch_run that also records the (nullable) CUDA events `ev_pyr0` /
+ * `ev_pyr1` around the pyramid launches and `ev_klt0` / `ev_klt1` around the
+ * tracking launch, for live per-kernel timing. */
+VT_API vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void *ev_pyr1, void *ev_klt0,
+                                    void *ev_klt1);
+
+/* Launch shape of the staged run and the number of kernel launches per run. */
+VT_API vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
+                               int *launches_per_run);
 
 /* Human-readable name of a status code. */
 VT_API const char *vt_status_str(vt_status s);

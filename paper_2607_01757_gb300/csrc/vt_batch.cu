@@ -1,0 +1,415 @@
+// Batched tracking (K5): many frames and tracking tasks of independent camera
+// streams in a fixed sequence of persistent launches.
+//
+//   H2D   job tables (pinned staging -> device, one copy)
+//   K1+K2 per pyramid level: one persistent launch over the tiles of every
+//         frame that has that level (level 0 also copies the caller image)
+//   K2    Scharr of each frame's last level
+//   K3    one persistent KLT launch: warps take points from a device work
+//         counter (one atomicAdd per point) across all tasks
+//
+// Grid sizes do not depend on the batch (SMs x resident CTAs), so one CUDA
+// graph per topology (deepest pyramid, gradient type, window) replays any
+// batch: the host only rewrites the pinned tables between replays.  Two
+// staging buffers let the host prepare run t+1 while run t executes.
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+
+#include "vt_klt.cuh"
+
+namespace vt {
+
+template <int WIN, int GT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, WIN <= 21 ? 16 / WARPS : (WARPS == 4 ? 3 : 1))
+    k_klt_batch(const uint8_t *tab, int *counter) {
+    const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
+    const BTask *tasks = reinterpret_cast<const BTask *>(tab + H->off_tasks);
+    const int *p0s = reinterpret_cast<const int *>(tab + H->off_prefix);
+    const int total = H->total_points, nt = H->ntasks;
+    const KParams P = H->P;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(counter, 1);
+        p = __shfl_sync(kFull, p, 0);
+        if (p >= total) break;
+        int lo = 0, hi = nt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(p0s + mid) <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const BTask &t = tasks[lo];
+        const int i = p - t.p0;
+        const float2 u = t.pts_in[i];
+        KParams Pt = P;
+        Pt.levels = t.levels;
+        KOut o;
+        track_point_dir<WIN, GT>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, o);
+        if (lane == 0) {
+            t.pts_out[i] = make_float2(o.x, o.y);
+            t.status[i] = (uint8_t)o.status;
+            if (t.err) t.err[i] = o.status ? o.err : 0.f;
+            if (t.reason) t.reason[i] = (uint8_t)o.reason;
+            if (t.flops) t.flops[i] = klt_flops(WIN, o);
+        }
+    }
+}
+
+typedef void (*KltBatchFn)(const uint8_t *, int *);
+
+template <int GT, int WARPS>
+static KltBatchFn klt_batch_fn(int win) {
+    switch (win) {
+        case 9: return k_klt_batch<9, GT, WARPS>;
+        case 15: return k_klt_batch<15, GT, WARPS>;
+        case 21: return k_klt_batch<21, GT, WARPS>;
+        case 31: return k_klt_batch<31, GT, WARPS>;
+    }
+    return nullptr;
+}
+
+static KltBatchFn klt_batch_kernel(int win, int gtype, int warps) {
+    if (gtype == VT_GRAD_F16) return warps == 8 ? klt_batch_fn<VT_GRAD_F16, 8>(win) : klt_batch_fn<VT_GRAD_F16, 4>(win);
+    return warps == 8 ? klt_batch_fn<VT_GRAD_S16, 8>(win) : klt_batch_fn<VT_GRAD_S16, 4>(win);
+}
+
+struct Topo {
+    int maxL, gtype, win, klt_warps, klt_grid, pyr_grid;
+    bool operator==(const Topo &o) const {
+        return maxL == o.maxL && gtype == o.gtype && win == o.win && klt_warps == o.klt_warps &&
+               klt_grid == o.klt_grid && pyr_grid == o.pyr_grid;
+    }
+};
+
+}  // namespace vt
+
+using namespace vt;
+
+struct vt_batch {
+    int cap_frames, cap_tasks;
+    size_t tab_bytes;
+    uint8_t *host[2];
+    uint8_t *dev[2];
+    int *counter;  // [2]
+    cudaEvent_t ev[2];
+    bool ev_used[2];
+    int next;    // buffer the next vt_batch_set writes
+    int staged;  // buffer with the latest staged tables, -1 if none
+    Topo topo[2];
+    cudaGraphExec_t exec[2];
+    Topo exec_topo[2];
+    cudaStream_t cap;
+    int sms;
+    int klt_warps;        // warps per CTA of the KLT launch (4 or 8)
+    int klt_ctas_per_sm;  // 0 = occupancy limit
+    int pyr_grid;
+};
+
+namespace vt {
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks, int &off_prefix, size_t &bytes) {
+    size_t o = align_up(sizeof(BatchHdr), 64);
+    off_frames = (int)o;
+    o = align_up(o + sizeof(BFrame) * F, 64);
+    off_jobs = (int)o;
+    o = align_up(o + sizeof(BLvlJob) * (size_t)F * VT_MAX_LEVELS, 64);
+    off_tasks = (int)o;
+    o = align_up(o + sizeof(BTask) * T, 64);
+    off_prefix = (int)o;
+    o = align_up(o + sizeof(int) * T, 256);
+    bytes = o;
+}
+
+static int klt_grid(const vt_batch *b, int win, int gtype) {
+    KltBatchFn fn = klt_batch_kernel(win, gtype, b->klt_warps);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)fn, b->klt_warps * 32, 0);
+    if (occ < 1) occ = 1;
+    const int per = b->klt_ctas_per_sm > 0 && b->klt_ctas_per_sm < occ ? b->klt_ctas_per_sm : occ;
+    return b->sms * per;
+}
+
+static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+    const Topo &tp = b->topo[k];
+    if (cudaMemcpyAsync(b->dev[k], b->host[k], b->tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(b->counter + k, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    if (ev && ev[0]) cudaEventRecord(ev[0], s);
+    vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, tp.pyr_grid, s);
+    if (st != VT_OK) return st;
+    if (ev && ev[1]) cudaEventRecord(ev[1], s);
+    KltBatchFn fn = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
+    if (!fn) return VT_ERR_ARG;
+    if (ev && ev[2]) cudaEventRecord(ev[2], s);
+    fn<<<tp.klt_grid, tp.klt_warps * 32, 0, s>>>(b->dev[k], b->counter + k);
+    if (ev && ev[3]) cudaEventRecord(ev[3], s);
+    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+}
+
+}  // namespace vt
+
+extern "C" {
+
+vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out) {
+    if (!out || max_frames < 0 || max_tasks < 0 || max_frames > (1 << 16) || max_tasks > (1 << 20)) return VT_ERR_ARG;
+    vt_batch *b = (vt_batch *)calloc(1, sizeof(vt_batch));
+    if (!b) return VT_ERR_OOM;
+    b->cap_frames = max_frames > 0 ? max_frames : 1;
+    b->cap_tasks = max_tasks > 0 ? max_tasks : 1;
+    int of, oj, ot, op;
+    layout(b->cap_frames, b->cap_tasks, of, oj, ot, op, b->tab_bytes);
+    bool ok = true;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && cudaMallocHost((void **)&b->host[k], b->tab_bytes) == cudaSuccess;
+        ok = ok && cudaMalloc((void **)&b->dev[k], b->tab_bytes) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc((void **)&b->counter, 2 * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    ok = ok && cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        vt_batch_free(b);
+        return VT_ERR_OOM;
+    }
+    b->klt_warps = 4;
+    b->klt_ctas_per_sm = 0;
+    b->pyr_grid = b->sms * (pyr_batch_blocks_per_sm() > 0 ? pyr_batch_blocks_per_sm() : 1);
+    b->staged = -1;
+    *out = b;
+    return VT_OK;
+}
+
+void vt_batch_free(vt_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    for (int k = 0; k < 2; ++k) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        if (b->host[k]) cudaFreeHost(b->host[k]);
+        if (b->dev[k]) cudaFree(b->dev[k]);
+        if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    }
+    if (b->counter) cudaFree(b->counter);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    free(b);
+}
+
+vt_status vt_batch_config(vt_batch *b, int klt_warps_per_cta, int klt_ctas_per_sm, int pyr_ctas) {
+    if (!b || (klt_warps_per_cta != 4 && klt_warps_per_cta != 8) || klt_ctas_per_sm < 0 || pyr_ctas < 0)
+        return VT_ERR_ARG;
+    b->klt_warps = klt_warps_per_cta;
+    b->klt_ctas_per_sm = klt_ctas_per_sm;
+    const int occ = pyr_batch_blocks_per_sm() > 0 ? pyr_batch_blocks_per_sm() : 1;
+    b->pyr_grid = pyr_ctas > 0 ? pyr_ctas : b->sms * occ;
+    return VT_OK;
+}
+
+vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_grad_type gtype,
+                       const vt_track_task *tasks, int ntasks, const vt_klt_params *prm) {
+    if (!b || !prm || nframes < 0 || ntasks < 0 || nframes > b->cap_frames || ntasks > b->cap_tasks)
+        return VT_ERR_ARG;
+    if ((nframes > 0 && !frames) || (ntasks > 0 && !tasks)) return VT_ERR_ARG;
+    if (gtype != VT_GRAD_S16 && gtype != VT_GRAD_F16) return VT_ERR_ARG;
+    if (!window_supported(prm->win) || prm->levels < 0 || prm->levels > VT_MAX_LEVELS || prm->max_iters < 1 ||
+        !(prm->eps >= 0.f) || !(prm->min_eig >= 0.f) || !(prm->fb_thr >= 0.f))
+        return VT_ERR_ARG;
+    // validate everything before touching the staging buffer
+    for (int f = 0; f < nframes; ++f) {
+        const vt_frame_job &fj = frames[f];
+        if (!fj.img || !fj.pyr || fj.pitch < fj.pyr->w) return VT_ERR_ARG;
+        for (int g = 0; g < f; ++g)
+            if (frames[g].pyr == fj.pyr) return VT_ERR_ARG;  // one build per pyramid per run
+    }
+    for (int t = 0; t < ntasks; ++t) {
+        const vt_track_task &tk = tasks[t];
+        if (!tk.prev || !tk.cur || tk.n < 0 || (tk.n > 0 && (!tk.pts_in || !tk.pts_out || !tk.status)))
+            return VT_ERR_ARG;
+        const int L = tk.levels > 0 ? tk.levels : prm->levels;
+        if (tk.levels < 0 || L > tk.prev->levels || L > tk.cur->levels) return VT_ERR_ARG;
+        auto gt_after = [&](const vt_pyramid *p) {
+            for (int f = 0; f < nframes; ++f)
+                if (frames[f].pyr == p) return (int)gtype;
+            return p->gtype;
+        };
+        if (gt_after(tk.prev) != (int)gtype || (tk.fb && gt_after(tk.cur) != (int)gtype)) return VT_ERR_ARG;
+    }
+    const int k = b->next;
+    if (b->ev_used[k]) {
+        if (cudaEventSynchronize(b->ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_CUDA;
+        }
+    }
+    uint8_t *tab = b->host[k];
+    BatchHdr *H = reinterpret_cast<BatchHdr *>(tab);
+    memset(H, 0, sizeof(BatchHdr));
+    size_t bytes;
+    layout(b->cap_frames, b->cap_tasks, H->off_frames, H->off_jobs, H->off_tasks, H->off_prefix, bytes);
+    H->cap_frames = b->cap_frames;
+    H->cap_tasks = b->cap_tasks;
+    H->nframes = nframes;
+    H->ntasks = ntasks;
+    H->P.win = prm->win;
+    H->P.levels = prm->levels;
+    H->P.max_iters = prm->max_iters;
+    H->P.eps2 = prm->eps * prm->eps;
+    H->P.min_eig = prm->min_eig;
+    H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
+    BFrame *bf = reinterpret_cast<BFrame *>(tab + H->off_frames);
+    BLvlJob *jobs = reinterpret_cast<BLvlJob *>(tab + H->off_jobs);
+    int maxL = 1;
+    for (int f = 0; f < nframes; ++f) {
+        const vt_frame_job &fj = frames[f];
+        vt_pyramid *p = fj.pyr;
+        bf[f].img = fj.img;
+        bf[f].lv = p->dev_lv;
+        bf[f].pitch = fj.pitch;
+        bf[f].vec_ok = ((uintptr_t)fj.img % 16 == 0) && (fj.pitch % 16 == 0);
+        bf[f].levels = p->levels;
+        p->gtype = (int)gtype;
+        if (p->levels > maxL) maxL = p->levels;
+    }
+    for (int l = 0; l < VT_MAX_LEVELS; ++l) {
+        BLvlJob *lj = jobs + (size_t)l * b->cap_frames;
+        int nj = 0, tiles = 0;
+        for (int f = 0; f < nframes; ++f) {
+            const vt_pyramid *p = frames[f].pyr;
+            int tx, nt;
+            if (l < VT_MAX_LEVELS - 1) {
+                if (p->levels <= l + 1) continue;
+                nt = pyr_tiles(p->lv[l].w, p->lv[l].h, tx);
+            } else {
+                nt = scharr_tiles(p->lv[p->levels - 1].w, p->lv[p->levels - 1].h, tx);
+            }
+            lj[nj].frame = f;
+            lj[nj].tiles_x = tx;
+            lj[nj].tile0 = tiles;
+            tiles += nt;
+            ++nj;
+        }
+        H->njobs[l] = nj;
+        H->ntiles[l] = tiles;
+    }
+    BTask *bt = reinterpret_cast<BTask *>(tab + H->off_tasks);
+    int *p0s = reinterpret_cast<int *>(tab + H->off_prefix);
+    long total = 0;
+    for (int t = 0; t < ntasks; ++t) {
+        const vt_track_task &tk = tasks[t];
+        bt[t].I = tk.prev->dev_lv;
+        bt[t].J = tk.cur->dev_lv;
+        bt[t].pts_in = reinterpret_cast<const float2 *>(tk.pts_in);
+        bt[t].pts_out = reinterpret_cast<float2 *>(tk.pts_out);
+        bt[t].status = tk.status;
+        bt[t].err = tk.err;
+        bt[t].reason = tk.reason;
+        bt[t].flops = tk.flops;
+        bt[t].n = tk.n;
+        bt[t].fb = tk.fb ? 1 : 0;
+        bt[t].levels = tk.levels > 0 ? tk.levels : prm->levels;
+        bt[t].p0 = (int)total;
+        p0s[t] = (int)total;
+        total += tk.n;
+    }
+    if (total > 0x7fffffff) return VT_ERR_ARG;
+    H->total_points = (int)total;
+    H->maxL = maxL;
+    Topo &tp = b->topo[k];
+    tp.maxL = maxL;
+    tp.gtype = (int)gtype;
+    tp.win = prm->win;
+    tp.klt_warps = b->klt_warps;
+    tp.klt_grid = klt_grid(b, prm->win, (int)gtype);
+    tp.pyr_grid = b->pyr_grid;
+    b->staged = k;
+    b->next = k ^ 1;
+    return VT_OK;
+}
+
+vt_status vt_batch_run(vt_batch *b, void *cuda_stream) {
+    if (!b || b->staged < 0) return VT_ERR_ARG;
+    const int k = b->staged;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    vt_status st = enqueue(b, k, s);
+    if (st != VT_OK) return st;
+    if (cudaEventRecord(b->ev[k], s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    b->ev_used[k] = true;
+    return VT_OK;
+}
+
+vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void *ev_pyr1, void *ev_klt0,
+                             void *ev_klt1) {
+    if (!b || b->staged < 0) return VT_ERR_ARG;
+    const int k = b->staged;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t ev[4] = {(cudaEvent_t)ev_pyr0, (cudaEvent_t)ev_pyr1, (cudaEvent_t)ev_klt0, (cudaEvent_t)ev_klt1};
+    vt_status st = enqueue(b, k, s, ev);
+    if (st != VT_OK) return st;
+    if (cudaEventRecord(b->ev[k], s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    b->ev_used[k] = true;
+    return VT_OK;
+}
+
+vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
+    if (!b || b->staged < 0) return VT_ERR_ARG;
+    const int k = b->staged;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!b->exec[k] || !(b->exec_topo[k] == b->topo[k])) {
+        if (b->exec[k]) {
+            cudaGraphExecDestroy(b->exec[k]);
+            b->exec[k] = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_CUDA;
+        }
+        vt_status st = enqueue(b, k, b->cap);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (st != VT_OK || e != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            return st != VT_OK ? st : VT_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&b->exec[k], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->exec[k] = nullptr;
+            return VT_ERR_CUDA;
+        }
+        b->exec_topo[k] = b->topo[k];
+    }
+    if (cudaGraphLaunch(b->exec[k], s) != cudaSuccess || cudaEventRecord(b->ev[k], s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    b->ev_used[k] = true;
+    return VT_OK;
+}
+
+vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
+                        int *launches_per_run) {
+    if (!b) return VT_ERR_ARG;
+    const int k = b->staged >= 0 ? b->staged : 0;
+    if (klt_grid_ctas) *klt_grid_ctas = b->topo[k].klt_grid;
+    if (klt_warps_per_cta) *klt_warps_per_cta = b->topo[k].klt_warps;
+    if (pyr_grid_ctas) *pyr_grid_ctas = b->topo[k].pyr_grid;
+    if (launches_per_run) *launches_per_run = b->staged >= 0 ? (b->topo[k].maxL - 1) + 1 + 1 : 0;
+    return VT_OK;
+}
+
+}  // extern "C"

@@ -28,6 +28,7 @@ struct vt_pyramid {
     void *base;  // single device allocation holding every level and plane
     size_t bytes;
     vt::Level lv[VT_MAX_LEVELS];
+    vt::Level *dev_lv;  // device copy of lv[] (written once at allocation)
 };
 
 namespace vt {
@@ -82,7 +83,60 @@ struct GradJobs {
     GradJob j[kMaxJobs];
 };
 
+// Tracking parameters as the kernels use them.
+struct KParams {
+    int win, levels, max_iters;
+    float eps2;     // eps^2
+    float min_eig;  // threshold on lambda_min / (win^2 255^2)
+    float fb_thr2;  // fb_thr^2
+};
+
+// ------------------------------------------------------- batched job tables
+// Device-side tables of one batched run (vt_batch): a header followed by the
+// frame, per-level job, task and task-prefix arrays at the header's offsets.
+struct BFrame {
+    const uint8_t *img;  // caller image (level-0 source)
+    const Level *lv;     // device level table of the destination pyramid
+    int pitch;
+    int vec_ok;  // img and pitch 16-byte aligned
+    int levels;
+    int pad;
+};
+
+struct BLvlJob {
+    int frame;
+    int tiles_x;
+    int tile0;  // first tile of this job within its launch
+    int pad;
+};
+
+struct BTask {
+    const Level *I;  // template pyramid (device level table)
+    const Level *J;  // target pyramid
+    const float2 *pts_in;
+    float2 *pts_out;
+    uint8_t *status;
+    float *err;
+    uint8_t *reason;
+    int32_t *flops;
+    int n, fb, p0, levels;
+};
+
+struct BatchHdr {
+    int nframes, ntasks, total_points, maxL;
+    int njobs[VT_MAX_LEVELS];   // [l < VT_MAX_LEVELS-1]: pyramid launch l; [VT_MAX_LEVELS-1]: last-level Scharr
+    int ntiles[VT_MAX_LEVELS];
+    int cap_frames, cap_tasks;
+    int off_frames, off_jobs, off_tasks, off_prefix;
+    KParams P;
+};
+
 // Host helpers implemented in vt_pyramid.cu.
+vt_status launch_pyr_batch(const uint8_t *dev_tab, int maxL, int gtype, int grid_pyr, int grid_sc, cudaStream_t s);
+int pyr_batch_blocks_per_sm();
+int pyr_tiles(int w, int h, int &tiles_x);
+int scharr_tiles(int w, int h, int &tiles_x);
+bool window_supported(int win);
 vt_status launch_pyrdown(const PyrJobs &jobs, int total_blocks, int gtype, cudaStream_t s);
 vt_status launch_scharr(const GradJobs &jobs, int total_blocks, int gtype, cudaStream_t s);
 void add_pyr_job(PyrJobs &jobs, int &blocks, const Level &src, const Level &dst, bool with_grad);

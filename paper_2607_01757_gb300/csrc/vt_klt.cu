@@ -18,6 +18,7 @@ struct KltArgs {
     uint8_t *reason;
     int32_t *iters;
     float *lmin;
+    int32_t *flops;
     KParams P;
 };
 
@@ -33,14 +34,10 @@ __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt
     if (pt >= A.n) return;
     const float2 p = A.pts_in[pt];
     KOut o;
-    if (FB) {
-        track_point_fb<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, lane, o);
-    } else {
-        float2 g = make_float2(0.f, 0.f);
-        const bool hg = A.guess != nullptr;
-        if (hg) g = A.guess[pt];
-        track_point<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, hg, g.x, g.y, lane, o);
-    }
+    float2 g = make_float2(0.f, 0.f);
+    const bool hg = !FB && A.guess != nullptr;
+    if (hg) g = A.guess[pt];
+    track_point_dir<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, FB, hg, g.x, g.y, lane, o);
     if (lane == 0) {
         A.pts_out[pt] = make_float2(o.x, o.y);
         A.status[pt] = (uint8_t)o.status;
@@ -48,6 +45,7 @@ __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt
         if (A.reason) A.reason[pt] = (uint8_t)o.reason;
         if (A.iters) A.iters[pt] = o.iters;
         if (A.lmin) A.lmin[pt] = o.lmin;
+        if (A.flops) A.flops[pt] = klt_flops(WIN, o);
     }
 }
 
@@ -108,6 +106,7 @@ static vt_status track_common(const vt_pyramid *prev, const vt_pyramid *cur, con
     A.reason = diag ? diag->reason : nullptr;
     A.iters = diag ? diag->iters : nullptr;
     A.lmin = diag ? diag->lmin : nullptr;
+    A.flops = diag ? diag->flops : nullptr;
     A.P.win = prm->win;
     A.P.levels = prm->levels;
     A.P.max_iters = prm->max_iters;

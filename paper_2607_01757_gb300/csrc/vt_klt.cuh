@@ -30,21 +30,23 @@ struct KPyr {
     Level lv[VT_MAX_LEVELS];
 };
 
-struct KParams {
-    int win, levels, max_iters;
-    float eps2;     // eps^2
-    float min_eig;  // threshold on lambda_min / (win^2 255^2)
-    float fb_thr2;  // fb_thr^2
-};
-
 struct KOut {
     float x, y;     // level-0 result (last estimate when lost)
     float err;      // mean |T - J| (0 when lost)
     float lmin;     // normalised lambda_min at the last level examined
     int status;     // 1 tracked
     int reason;     // VT_TRACKED / VT_LOST_*
-    int iters;      // Newton iterations over all levels
+    int iters;      // Newton iterations over all levels (and both passes)
+    int tmpl;       // template extractions (window sweeps of 27 FLOP per sample)
+    int errp;       // error passes (window sweeps of 9 FLOP per sample)
 };
+
+// Algorithmic FLOPs of a tracked point: per window sample 27 for a template
+// sweep (bilinear I, Ix, Iy: 3 x 7; G: 3 FMA), 12 for a Newton sweep
+// (bilinear J: 7; residual: 1; b: 2 FMA) and 9 for the error sweep.
+__device__ __forceinline__ int klt_flops(int win, const KOut &o) {
+    return win * win * (27 * o.tmpl + 12 * o.iters + 9 * o.errp);
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -178,6 +180,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     o.status = 1;
     o.reason = VT_TRACKED;
     o.iters = 0;
+    o.tmpl = 0;
+    o.errp = 0;
     o.err = 0.f;
     o.lmin = __int_as_float(0x7fc00000);
     if (!(ux0 >= 0.f && ux0 <= (float)(I[0].w - 1) && uy0 >= 0.f && uy0 <= (float)(I[0].h - 1))) {
@@ -198,6 +202,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         const float s = pow2neg(l);
         const float ux = ux0 * s, uy = uy0 * s;
         load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY);
+        ++o.tmpl;
         float a11 = 0.f, a12 = 0.f, a22 = 0.f;
 #pragma unroll
         for (int r = 0; r < WIN; ++r) {
@@ -273,27 +278,48 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             float e, unused;
             residual_pass<WIN, true>(J[0], o.x, o.y, lane, T, GX, GY, e, unused);
             o.err = e / N;
+            ++o.errp;
         }
     }
 }
 
-// Forward I->J, backward J->I from the forward result, FB test.
+// Forward I->J (pass 0) and, with fb, backward J->I from the forward result
+// (pass 1) followed by the FB test.  One inlined copy of track_point serves
+// both passes, and every kernel (single-pair or batched) calls this function,
+// so a point's result does not depend on which kernel tracked it.
 template <int WIN, int GT>
-__device__ __forceinline__ void track_point_fb(const Level *I, const Level *J, const KParams &P, float ux0,
-                                               float uy0, int lane, KOut &o) {
-    track_point<WIN, GT>(I, J, P, ux0, uy0, false, 0.f, 0.f, lane, o);
-    if (!o.status) return;
-    KOut b;
-    track_point<WIN, GT>(J, I, P, o.x, o.y, false, 0.f, 0.f, lane, b);
-    if (!b.status) {
-        o.status = 0;
-        o.reason = b.reason;
-        return;
-    }
-    const float dx = ux0 - b.x, dy = uy0 - b.y;
-    if (!(dx * dx + dy * dy <= P.fb_thr2)) {
-        o.status = 0;
-        o.reason = VT_LOST_FB;
+__device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, const KParams &P, float ux0,
+                                                float uy0, bool fb, bool has_guess, float gux, float guy, int lane,
+                                                KOut &o) {
+    const Level *A = I, *B = J;
+    float x = ux0, y = uy0;
+    const int npass = fb ? 2 : 1;
+#pragma unroll 1
+    for (int pass = 0; pass < npass; ++pass) {
+        KOut r;
+        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, r);
+        if (pass == 0) {
+            o = r;
+            if (!r.status) return;
+            x = r.x;
+            y = r.y;
+            A = J;
+            B = I;
+        } else {
+            o.iters += r.iters;
+            o.tmpl += r.tmpl;
+            o.errp += r.errp;
+            if (!r.status) {
+                o.status = 0;
+                o.reason = r.reason;
+                return;
+            }
+            const float dx = ux0 - r.x, dy = uy0 - r.y;
+            if (!(dx * dx + dy * dy <= P.fb_thr2)) {
+                o.status = 0;
+                o.reason = VT_LOST_FB;
+            }
+        }
     }
 }
 

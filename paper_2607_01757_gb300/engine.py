@@ -1,0 +1,164 @@
+"""Host runtime of the batched tracking path: per-stream device state and the
+per-step job tables of vt_batch.
+
+A camera stream keeps two left pyramids (previous / current, swapped by
+index, never copied), one right pyramid when it is stereo, fixed device input
+slots for the incoming frames and output buffers for its tracking tasks.
+One step of a stream with new frame(s):
+
+  mono:   build cur-left; track prev-left -> cur-left (forward, backward, FB)
+  stereo: build cur-left and right; track prev-left -> cur-left and
+          cur-left -> right (the cross-camera check), both with FB
+
+All streams of a step go into one vt_batch run (persistent launches, CUDA
+graph).  The plain path issues the same work as single-pair calls, one
+stream after another.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+from . import vt
+
+
+@dataclass
+class StreamState:
+    sid: int
+    w: int
+    h: int
+    levels: int
+    stereo: bool
+    n_max: int
+    pyr: list = field(default_factory=list)  # two left pyramids
+    pyr_r: object = None
+    in_left: object = None  # device input slot [h, w] uint8
+    in_right: object = None
+    kp_t: object = None  # device float2 [n_max]: points tracked prev -> cur
+    kp_s: object = None  # device float2 [n_max]: points tracked left -> right
+    out_t: tuple = ()  # (pts, status, err)
+    out_s: tuple = ()
+    built: int = 0  # number of frames built so far (cur index = built % 2 after a build)
+
+
+class BatchedTracker:
+    """Many independent camera streams tracked one step at a time."""
+
+    def __init__(self, specs, params: vt.KltParams, grad_type: int = vt.VT_GRAD_S16, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.params = params
+        self.grad_type = grad_type
+        self.streams = []
+        for sp in specs:
+            s = StreamState(sp.sid, sp.w, sp.h, sp.levels, sp.stereo, sp.n_kp)
+            s.pyr = [vt.vt_pyramid_create(sp.w, sp.h, sp.levels) for _ in range(2)]
+            s.pyr_r = vt.vt_pyramid_create(sp.w, sp.h, sp.levels) if sp.stereo else None
+            s.in_left = torch.zeros((sp.h, sp.w), dtype=torch.uint8, device=device)
+            s.in_right = torch.zeros((sp.h, sp.w), dtype=torch.uint8, device=device) if sp.stereo else None
+            s.kp_t = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device)
+            s.kp_s = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device) if sp.stereo else None
+            mk = lambda: (torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device),  # noqa: E731
+                          torch.zeros(sp.n_kp, dtype=torch.uint8, device=device),
+                          torch.zeros(sp.n_kp, dtype=torch.float32, device=device))
+            s.out_t = mk()
+            s.out_s = mk() if sp.stereo else ()
+            self.streams.append(s)
+        nf = sum(2 if s.stereo else 1 for s in self.streams)
+        self.batch = vt.Batch(max(1, nf), max(1, nf))
+        self._flops = None
+
+    # ------------------------------------------------------------ descriptors
+    def step_tables(self, sids, n_t, n_s, left=None, right=None, flops=None, kpt=None, kps=None):
+        """ctypes arrays (frames, tasks) of one step for streams `sids`.
+
+        n_t / n_s: point counts of the temporal / stereo task per stream;
+        left / right: per-stream device images to build from (default: the
+        stream's input slots); kpt / kps: per-stream device point arrays
+        (default: the stream's point buffers); flops: optional per-stream
+        (t, s) int32 arrays."""
+        frames, tasks = [], []
+        for k, i in enumerate(sids):
+            s = self.streams[i]
+            cur = s.pyr[(s.built + 1) % 2]
+            frames.append(vt.frame_job(left[k] if left is not None else s.in_left, cur))
+            if s.stereo:
+                frames.append(vt.frame_job(right[k] if right is not None else s.in_right, s.pyr_r))
+        for k, i in enumerate(sids):
+            s = self.streams[i]
+            prev, cur = s.pyr[s.built % 2], s.pyr[(s.built + 1) % 2]
+            if n_t[k] > 0:
+                fl = flops[k][0] if flops is not None else None
+                pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
+                tasks.append(vt.track_task(prev, cur, pts, s.out_t[0], s.out_t[1], s.out_t[2], fb=True, flops=fl,
+                                           levels=s.levels))
+            if s.stereo and n_s[k] > 0:
+                fl = flops[k][1] if flops is not None else None
+                pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
+                tasks.append(vt.track_task(cur, s.pyr_r, pts, s.out_s[0], s.out_s[1], s.out_s[2], fb=True, flops=fl,
+                                           levels=s.levels))
+        fa = (vt.vt_frame_job * max(1, len(frames)))(*frames)
+        ta = (vt.vt_track_task * max(1, len(tasks)))(*tasks)
+        return fa, len(frames), ta, len(tasks)
+
+    def stage(self, tables):
+        fa, nf, ta, nt = tables
+        prm = self.params.c()
+        code = vt._lib.vt_batch_set(self.batch, fa, nf, self.grad_type, ta, nt, C.byref(prm))
+        if code != vt.VT_OK:
+            raise vt.VTError("vt_batch_set", code)
+
+    def advance(self, sids):
+        """After a step has been issued: the current pyramid becomes previous."""
+        for i in sids:
+            self.streams[i].built += 1
+
+    def run(self, stream=None, graph=True, events=None):
+        if events is not None:
+            vt.vt_batch_run_timed(self.batch, stream, *events)
+        elif graph:
+            vt.vt_batch_run_graph(self.batch, stream)
+        else:
+            vt.vt_batch_run(self.batch, stream)
+
+    # ------------------------------------------------------------- plain path
+    def plain_step(self, sids, n_t, n_s, left=None, right=None, stream=None, kpt=None, kps=None):
+        """The same step as single-pair calls, stream after stream."""
+        import copy
+
+        for k, i in enumerate(sids):
+            s = self.streams[i]
+            prm = copy.copy(self.params)
+            prm.levels = s.levels
+            prev, cur = s.pyr[s.built % 2], s.pyr[(s.built + 1) % 2]
+            vt.vt_pyramid_build_grad(left[k] if left is not None else s.in_left, s.levels, self.grad_type, stream,
+                                     out=cur)
+            if s.stereo:
+                vt.vt_pyramid_build_grad(right[k] if right is not None else s.in_right, s.levels, self.grad_type,
+                                         stream, out=s.pyr_r)
+            if n_t[k] > 0:
+                pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
+                vt.vt_klt_track_fb(prev, cur, pts, prm, s.out_t[0], s.out_t[1], s.out_t[2], stream=stream)
+            if s.stereo and n_s[k] > 0:
+                pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
+                vt.vt_klt_track_fb(cur, s.pyr_r, pts, prm, s.out_s[0], s.out_s[1], s.out_s[2], stream=stream)
+
+    def plain_launches(self, sids, n_t, n_s):
+        """Kernel launches of plain_step (the level-0 copy is a memcpy, not a kernel)."""
+        n = 0
+        for k, i in enumerate(sids):
+            s = self.streams[i]
+            per_pyr = (s.levels - 1) + 1
+            n += per_pyr * (2 if s.stereo else 1)
+            n += int(n_t[k] > 0) + int(s.stereo and n_s[k] > 0)
+        return n
+
+    def free(self):
+        self.batch.free()
+        for s in self.streams:
+            for p in s.pyr:
+                p.free()
+            if s.pyr_r is not None:
+                s.pyr_r.free()

@@ -53,7 +53,7 @@ class vt_klt_params(C.Structure):
 
 
 class vt_klt_diag(C.Structure):
-    _fields_ = [("reason", vp), ("iters", vp), ("lmin", vp)]
+    _fields_ = [("reason", vp), ("iters", vp), ("lmin", vp), ("flops", vp)]
 
 
 def _sig(name, res, args):
@@ -75,6 +75,7 @@ _sig("vt_klt_track_ex", i32, [vp, vp, vp, i32, vp, C.POINTER(vt_klt_params), vp,
                               C.POINTER(vt_klt_diag), vp])
 _sig("vt_klt_track_fb", i32, [vp, vp, vp, i32, C.POINTER(vt_klt_params), vp, vp, vp, C.POINTER(vt_klt_diag), vp])
 _sig("vt_fb_check", i32, [vp, vp, vp, vp, i32, f32, vp, vp])
+_sig("vt_pyramid_create", i32, [i32, i32, i32, C.POINTER(vp)])
 _sig("vt_status_str", C.c_char_p, [i32])
 _sig("vt_version", C.c_char_p, [])
 
@@ -244,10 +245,10 @@ class KltParams:
         return vt_klt_params(self.win, self.levels, self.max_iters, self.eps, self.min_eig, self.fb_thr)
 
 
-def _diag(reason=None, iters=None, lmin=None):
-    if reason is None and iters is None and lmin is None:
+def _diag(reason=None, iters=None, lmin=None, flops=None):
+    if reason is None and iters is None and lmin is None and flops is None:
         return None
-    return C.byref(vt_klt_diag(_ptr(reason), _ptr(iters), _ptr(lmin)))
+    return C.byref(vt_klt_diag(_ptr(reason), _ptr(iters), _ptr(lmin), _ptr(flops)))
 
 
 def vt_klt_track(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None, pts_guess=None, win=21,
@@ -258,23 +259,138 @@ def vt_klt_track(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None,
 
 
 def vt_klt_track_ex(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
-                    pts_guess=None, reason=None, iters=None, lmin=None, stream=None) -> None:
+                    pts_guess=None, reason=None, iters=None, lmin=None, flops=None, stream=None) -> None:
     n = int(pts_in.shape[0])
     prm = params.c()
     _check(_lib.vt_klt_track_ex(prev, cur, _ptr(pts_in), n, _ptr(pts_guess), C.byref(prm), _ptr(pts_out),
-                                _ptr(status), _ptr(err), _diag(reason, iters, lmin), _stream(stream)),
+                                _ptr(status), _ptr(err), _diag(reason, iters, lmin, flops), _stream(stream)),
            "vt_klt_track_ex")
 
 
 def vt_klt_track_fb(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
-                    reason=None, iters=None, lmin=None, stream=None) -> None:
+                    reason=None, iters=None, lmin=None, flops=None, stream=None) -> None:
     n = int(pts_in.shape[0])
     prm = params.c()
     _check(_lib.vt_klt_track_fb(prev, cur, _ptr(pts_in), n, C.byref(prm), _ptr(pts_out), _ptr(status),
-                                _ptr(err), _diag(reason, iters, lmin), _stream(stream)), "vt_klt_track_fb")
+                                _ptr(err), _diag(reason, iters, lmin, flops), _stream(stream)), "vt_klt_track_fb")
 
 
 def vt_fb_check(p0, p0_back, st_f, st_b, thr, status_out, stream=None) -> None:
     n = int(p0.shape[0])
     _check(_lib.vt_fb_check(_ptr(p0), _ptr(p0_back), _ptr(st_f), _ptr(st_b), n, thr, _ptr(status_out),
                             _stream(stream)), "vt_fb_check")
+
+
+def vt_pyramid_create(w: int, h: int, levels: int) -> Pyramid:
+    hd = vp()
+    _check(_lib.vt_pyramid_create(w, h, levels, C.byref(hd)), "vt_pyramid_create")
+    return Pyramid(hd.value)
+
+
+# ------------------------------------------------------------------ batched
+class vt_frame_job(C.Structure):
+    _fields_ = [("img", vp), ("pitch", i32), ("pyr", vp)]
+
+
+class vt_track_task(C.Structure):
+    _fields_ = [("prev", vp), ("cur", vp), ("pts_in", vp), ("n", i32), ("fb", i32), ("pts_out", vp),
+                ("status", vp), ("err", vp), ("reason", vp), ("flops", vp), ("levels", i32)]
+
+
+_sig("vt_batch_create", i32, [i32, i32, C.POINTER(vp)])
+_sig("vt_batch_free", None, [vp])
+_sig("vt_batch_config", i32, [vp, i32, i32, i32])
+_sig("vt_batch_set", i32, [vp, C.POINTER(vt_frame_job), i32, i32, C.POINTER(vt_track_task), i32,
+                           C.POINTER(vt_klt_params)])
+_sig("vt_batch_run", i32, [vp, vp])
+_sig("vt_batch_run_graph", i32, [vp, vp])
+_sig("vt_batch_run_timed", i32, [vp, vp, vp, vp, vp, vp])
+_sig("vt_batch_info", i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)])
+
+
+def _event_handle(ev):
+    """cudaEvent_t of a torch.cuda.Event (or an int handle, or None).  torch
+    creates its events lazily, so a torch event must have been recorded once."""
+    if ev is None or isinstance(ev, int):
+        return ev
+    h = ev.cuda_event
+    if not h:
+        raise ValueError("torch.cuda.Event has no CUDA event yet: record it once before passing it")
+    return h
+
+
+class Batch:
+    """Owning handle of a vt_batch (batched persistent tracking)."""
+
+    def __init__(self, max_frames: int, max_tasks: int):
+        hd = vp()
+        _check(_lib.vt_batch_create(max_frames, max_tasks, C.byref(hd)), "vt_batch_create")
+        self.handle = hd.value
+        self._keep = None
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+    def free(self):
+        if self.handle:
+            _lib.vt_batch_free(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def vt_batch_create(max_frames: int, max_tasks: int) -> Batch:
+    return Batch(max_frames, max_tasks)
+
+
+def vt_batch_free(b: Batch) -> None:
+    b.free()
+
+
+def vt_batch_config(b: Batch, klt_warps_per_cta: int = 4, klt_ctas_per_sm: int = 0, pyr_ctas: int = 0) -> None:
+    _check(_lib.vt_batch_config(b, klt_warps_per_cta, klt_ctas_per_sm, pyr_ctas), "vt_batch_config")
+
+
+def frame_job(img, pyr: Pyramid) -> vt_frame_job:
+    """Descriptor of one pyramid build from a 2-D uint8 device tensor."""
+    p, w, h, pitch, dev = _img_args(img)
+    if not dev:
+        raise ValueError("batched frames must be device images")
+    return vt_frame_job(p, pitch, pyr.handle)
+
+
+def track_task(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None, fb=True, reason=None,
+               flops=None, levels=0) -> vt_track_task:
+    return vt_track_task(prev.handle, cur.handle, _ptr(pts_in), int(pts_in.shape[0]), int(bool(fb)),
+                         _ptr(pts_out), _ptr(status), _ptr(err), _ptr(reason), _ptr(flops), int(levels))
+
+
+def vt_batch_set(b: Batch, frames, tasks, params: KltParams, grad_type: int = VT_GRAD_S16) -> None:
+    fa = (vt_frame_job * max(1, len(frames)))(*frames)
+    ta = (vt_track_task * max(1, len(tasks)))(*tasks)
+    prm = params.c()
+    _check(_lib.vt_batch_set(b, fa, len(frames), grad_type, ta, len(tasks), C.byref(prm)), "vt_batch_set")
+
+
+def vt_batch_run(b: Batch, stream=None) -> None:
+    _check(_lib.vt_batch_run(b, _stream(stream)), "vt_batch_run")
+
+
+def vt_batch_run_graph(b: Batch, stream=None) -> None:
+    _check(_lib.vt_batch_run_graph(b, _stream(stream)), "vt_batch_run_graph")
+
+
+def vt_batch_run_timed(b: Batch, stream=None, ev_pyr0=None, ev_pyr1=None, ev_klt0=None, ev_klt1=None) -> None:
+    _check(_lib.vt_batch_run_timed(b, _stream(stream), _event_handle(ev_pyr0), _event_handle(ev_pyr1),
+                                   _event_handle(ev_klt0), _event_handle(ev_klt1)), "vt_batch_run_timed")
+
+
+def vt_batch_info(b: Batch):
+    g, w, pg, nl = i32(), i32(), i32(), i32()
+    _check(_lib.vt_batch_info(b, C.byref(g), C.byref(w), C.byref(pg), C.byref(nl)), "vt_batch_info")
+    return dict(klt_grid=g.value, klt_warps=w.value, pyr_grid=pg.value, launches_per_run=nl.value)
