@@ -183,8 +183,11 @@ typedef struct vt_klt_diag {
     float *lmin;     /* normalised lambda_min of G at the last level examined
                         (forward pass) */
     int32_t *flops;  /* algorithmic FLOPs spent on the point: win^2 x (27 per
-                        template sweep + 12 per Newton sweep + 9 per error
+                        template sweep + 12 per Newton iteration + 9 per error
                         sweep), both passes in the fused calls */
+    int32_t *sweeps; /* footprint sweeps the Newton iterations executed (an
+                        iteration whose integer cell is unchanged reuses the
+                        previous sweep's moments) */
 } vt_klt_diag;
 
 /* vt_klt_track with an explicit parameter block and diagnostics (diag nullable). */

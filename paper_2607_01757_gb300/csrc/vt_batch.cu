@@ -21,8 +21,10 @@
 namespace vt {
 
 template <int WIN, int GT, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, WIN <= 21 ? 16 / WARPS : (WARPS == 4 ? 3 : 1))
+__global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARPS)
     k_klt_batch(const uint8_t *tab, int *counter) {
+    extern __shared__ __align__(16) uint8_t klt_smem[];
+    KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const BTask *tasks = reinterpret_cast<const BTask *>(tab + H->off_tasks);
     const int *p0s = reinterpret_cast<const int *>(tab + H->off_prefix);
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(WARPS * 32, WIN <= 21 ? 16 / WARPS : (WARPS ==
         KParams Pt = P;
         Pt.levels = t.levels;
         KOut o;
-        track_point_dir<WIN, GT>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, o);
+        track_point_dir<WIN, GT>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, sm, o);
         if (lane == 0) {
             t.pts_out[i] = make_float2(o.x, o.y);
             t.status[i] = (uint8_t)o.status;
@@ -59,18 +61,34 @@ __global__ void __launch_bounds__(WARPS * 32, WIN <= 21 ? 16 / WARPS : (WARPS ==
 
 typedef void (*KltBatchFn)(const uint8_t *, int *);
 
-template <int GT, int WARPS>
-static KltBatchFn klt_batch_fn(int win) {
-    switch (win) {
-        case 9: return k_klt_batch<9, GT, WARPS>;
-        case 15: return k_klt_batch<15, GT, WARPS>;
-        case 21: return k_klt_batch<21, GT, WARPS>;
-        case 31: return k_klt_batch<31, GT, WARPS>;
+struct KltBatchKernel {
+    KltBatchFn fn;
+    size_t smem;  // dynamic shared memory per CTA
+};
+
+template <int WIN, int GT, int WARPS>
+static KltBatchKernel klt_batch_entry() {
+    const size_t smem = WARPS * sizeof(KSmem<WIN>);
+    static bool attr = false;
+    if (!attr) {  // opt in to more than 48 KB where needed (idempotent)
+        cudaFuncSetAttribute(k_klt_batch<WIN, GT, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
     }
-    return nullptr;
+    return {k_klt_batch<WIN, GT, WARPS>, smem};
 }
 
-static KltBatchFn klt_batch_kernel(int win, int gtype, int warps) {
+template <int GT, int WARPS>
+static KltBatchKernel klt_batch_fn(int win) {
+    switch (win) {
+        case 9: return klt_batch_entry<9, GT, WARPS>();
+        case 15: return klt_batch_entry<15, GT, WARPS>();
+        case 21: return klt_batch_entry<21, GT, WARPS>();
+        case 31: return klt_batch_entry<31, GT, WARPS>();
+    }
+    return {nullptr, 0};
+}
+
+static KltBatchKernel klt_batch_kernel(int win, int gtype, int warps) {
     if (gtype == VT_GRAD_F16) return warps == 8 ? klt_batch_fn<VT_GRAD_F16, 8>(win) : klt_batch_fn<VT_GRAD_F16, 4>(win);
     return warps == 8 ? klt_batch_fn<VT_GRAD_S16, 8>(win) : klt_batch_fn<VT_GRAD_S16, 4>(win);
 }
@@ -125,9 +143,9 @@ static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks,
 }
 
 static int klt_grid(const vt_batch *b, int win, int gtype) {
-    KltBatchFn fn = klt_batch_kernel(win, gtype, b->klt_warps);
+    const KltBatchKernel kb = klt_batch_kernel(win, gtype, b->klt_warps);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)fn, b->klt_warps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)kb.fn, b->klt_warps * 32, kb.smem);
     if (occ < 1) occ = 1;
     const int per = b->klt_ctas_per_sm > 0 && b->klt_ctas_per_sm < occ ? b->klt_ctas_per_sm : occ;
     return b->sms * per;
@@ -144,10 +162,10 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
     vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, tp.pyr_grid, s);
     if (st != VT_OK) return st;
     if (ev && ev[1]) cudaEventRecord(ev[1], s);
-    KltBatchFn fn = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
-    if (!fn) return VT_ERR_ARG;
+    const KltBatchKernel kb = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
+    if (!kb.fn) return VT_ERR_ARG;
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
-    fn<<<tp.klt_grid, tp.klt_warps * 32, 0, s>>>(b->dev[k], b->counter + k);
+    kb.fn<<<tp.klt_grid, tp.klt_warps * 32, kb.smem, s>>>(b->dev[k], b->counter + k);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }

@@ -19,16 +19,14 @@ struct KltArgs {
     int32_t *iters;
     float *lmin;
     int32_t *flops;
+    int32_t *sweeps;
     KParams P;
-};
-
-template <int WIN>
-struct KltOcc {
-    static constexpr int min_blocks = WIN <= 21 ? 4 : 3;
 };
 
 template <int WIN, int GT, bool FB>
 __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt(const __grid_constant__ KltArgs A) {
+    extern __shared__ __align__(16) uint8_t klt_smem[];
+    KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
     const int pt = blockIdx.x * KLT_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (pt >= A.n) return;
@@ -37,7 +35,7 @@ __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt
     float2 g = make_float2(0.f, 0.f);
     const bool hg = !FB && A.guess != nullptr;
     if (hg) g = A.guess[pt];
-    track_point_dir<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, FB, hg, g.x, g.y, lane, o);
+    track_point_dir<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, FB, hg, g.x, g.y, lane, sm, o);
     if (lane == 0) {
         A.pts_out[pt] = make_float2(o.x, o.y);
         A.status[pt] = (uint8_t)o.status;
@@ -46,6 +44,7 @@ __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt
         if (A.iters) A.iters[pt] = o.iters;
         if (A.lmin) A.lmin[pt] = o.lmin;
         if (A.flops) A.flops[pt] = klt_flops(WIN, o);
+        if (A.sweeps) A.sweeps[pt] = o.sweeps;
     }
 }
 
@@ -61,7 +60,15 @@ __global__ void k_fb_check(const float2 *p0, const float2 *p1, const uint8_t *sf
 template <int WIN, int GT, bool FB>
 static vt_status launch_one(const KltArgs &A, cudaStream_t s) {
     const int blocks = (A.n + KLT_WARPS - 1) / KLT_WARPS;
-    k_klt<WIN, GT, FB><<<blocks, KLT_WARPS * 32, 0, s>>>(A);
+    const size_t smem = KLT_WARPS * sizeof(KSmem<WIN>);
+    if (smem > 48 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_klt<WIN, GT, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+    }
+    k_klt<WIN, GT, FB><<<blocks, KLT_WARPS * 32, smem, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 
@@ -107,6 +114,7 @@ static vt_status track_common(const vt_pyramid *prev, const vt_pyramid *cur, con
     A.iters = diag ? diag->iters : nullptr;
     A.lmin = diag ? diag->lmin : nullptr;
     A.flops = diag ? diag->flops : nullptr;
+    A.sweeps = diag ? diag->sweeps : nullptr;
     A.P.win = prm->win;
     A.P.levels = prm->levels;
     A.P.max_iters = prm->max_iters;

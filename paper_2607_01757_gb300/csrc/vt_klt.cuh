@@ -13,14 +13,19 @@
 //   result v = u + g_0 + nu (bound test), error = mean |T - J_0(v + x)|.
 //
 // Mapping to the warp: lane c owns window column c for every row (lanes
-// c <= win load, lanes c < win compute).  Every window sample shares the
-// same fractional bilinear weights, so a row is one coalesced load of
-// win + 1 consecutive bytes, the right neighbour comes from the next lane by
-// shuffle and the vertical blend reuses the previous row.  The template and
-// its gradients stay in registers (3 * win floats per lane).  Sums over the
-// window are per-lane FP32 sums over rows followed by an XOR butterfly, so
-// every lane holds bit-identical totals and control flow stays warp-uniform.
+// c <= win load, lanes c < win compute).  Every window sample of one Newton
+// iteration shares the same fractional bilinear weights (bx, by), so
+// b = sum (T - J(q + x)) grad T expands exactly into bx, by and eight moments
+// of the integer footprint of J under the window (cell_moments).  A sweep
+// over the footprint is needed only when the integer part of q changes;
+// iterations that stay in the same cell reuse the moments.  The template and
+// its gradients stay in registers (3 * win floats per lane); the footprint is
+// staged in per-warp shared memory.  Sums over the window are per-lane FP32
+// sums over rows followed by an XOR butterfly, so every lane holds
+// bit-identical totals and control flow stays warp-uniform.
 #pragma once
+
+#include <climits>
 
 #include "vt_internal.cuh"
 
@@ -39,6 +44,7 @@ struct KOut {
     int iters;      // Newton iterations over all levels (and both passes)
     int tmpl;       // template extractions (window sweeps of 27 FLOP per sample)
     int errp;       // error passes (window sweeps of 9 FLOP per sample)
+    int sweeps;     // footprint sweeps the Newton iterations actually needed
 };
 
 // Algorithmic FLOPs of a tracked point: per window sample 27 for a template
@@ -49,6 +55,13 @@ __device__ __forceinline__ int klt_flops(int win, const KOut &o) {
 }
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Resident CTAs per SM the tracking kernels are register-budgeted for
+// (4-warp CTAs): 4 for windows up to 21 (128 registers per thread).
+template <int WIN>
+struct KltOcc {
+    static constexpr int min_blocks = WIN <= 21 ? 4 : 3;
+};
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -80,8 +93,17 @@ __device__ __forceinline__ constexpr float grad_unit() { return GT == VT_GRAD_S1
 // 2^-l exactly.
 __device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
 
-// Sample the template (image and gradients) of level `L` around (ux, uy).
-// Lane c ends with column c of the window in T/GX/GY (zero for c >= WIN).
+// Per-warp shared scratch: the staged footprint of J for one window sweep
+// (win + 1 rows of NW 32-bit words).
+template <int WIN>
+struct KSmem {
+    static constexpr int NW = (WIN + 7) / 4;            // words per staged row: covers 3 + win + 1 bytes
+    static constexpr int JS = (NW * 4 + 15) / 16 * 16;  // staged row stride in bytes
+    uint8_t j[(WIN + 1) * JS];
+};
+
+// Sample the template of level `L` around (ux, uy): lane c ends with column
+// c of T and of its gradients (zero for c >= WIN).
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
                                               float (&GX)[WIN], float (&GY)[WIN]) {
@@ -126,48 +148,116 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
     }
 }
 
-// One pass over J_l at (qx, qy): b = sum r grad T (ABS = false) or
-// e = sum |r| over the window (ABS = true, returned in b1).
-template <int WIN, bool ABS>
-__device__ __forceinline__ void residual_pass(const Level &L, float qx, float qy, int lane, const float (&T)[WIN],
-                                              const float (&GX)[WIN], const float (&GY)[WIN], float &b1,
-                                              float &b2) {
-    constexpr int HW = WIN / 2;
-    const float fx = floorf(qx), fy = floorf(qy);
-    const float bx = qx - fx, by = qy - fy;
-    const int x0 = (int)fx - HW, y0 = (int)fy - HW;
-    const int col = clampi(x0 + lane, 0, L.w - 1);
-    const uint8_t *jb = L.img + col;
-    const bool ld = lane <= WIN;
-    float s1 = 0.f, s2 = 0.f, ph = 0.f;
+// Stage the (win + 1) x (win + 1) footprint of J with top-left (x0, y0) in
+// shared memory: 32-bit loads when it lies inside the image, byte loads with
+// clamped (replicated) indices near the border.  Returns the byte offset of
+// column 0 within a staged row.
+template <int WIN>
+__device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, int lane, KSmem<WIN> &sm) {
+    constexpr int NW = KSmem<WIN>::NW, JS = KSmem<WIN>::JS;
+    int off;
+    __syncwarp();  // every lane is done with the previous footprint
+    if (x0 >= 0 && y0 >= 0 && x0 + WIN < L.w && y0 + WIN < L.h) {
+        const int wx0 = x0 & ~3;
+        off = x0 - wx0;
+        const uint8_t *base = L.img + (size_t)y0 * L.pitch + wx0;
+        for (int k = lane; k < (WIN + 1) * NW; k += 32) {
+            const int row = k / NW, wc = k - row * NW;
+            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(base + (size_t)row * L.pitch) + wc);
+            *reinterpret_cast<uint32_t *>(&sm.j[row * JS + 4 * wc]) = w;
+        }
+    } else {
+        off = 0;
+        for (int k = lane; k < (WIN + 1) * (WIN + 1); k += 32) {
+            const int row = k / (WIN + 1), c = k - row * (WIN + 1);
+            sm.j[row * JS + c] = __ldg(L.img + (size_t)clampi(y0 + row, 0, L.h - 1) * L.pitch +
+                                       clampi(x0 + c, 0, L.w - 1));
+        }
+    }
+    __syncwarp();
+    return off;
+}
+
+// Moments of one integer footprint F (top-left (x0, y0)) against the template.
+// With F00 = F(y, x), F01 = F(y, x+1), F10 = F(y+1, x), F11 = F(y+1, x+1) for
+// window sample (y, x), the bilinear sample at fractional offset (bx, by) is
+//   F00 + bx (F01 - F00) + by (F10 - F00) + bx by (F11 - F10 - F01 + F00),
+// so for every q with floor(q) = (x0, y0) + (h, h):
+//   sum r grad T = R - bx Sx - by Sy - bx by Sxy,
+//   R = sum (T - F00) grad T, Sx = sum (F01 - F00) grad T,
+//   Sy = sum (F10 - F00) grad T, Sxy = sum (F11 - F10 - F01 + F00) grad T.
+// The footprint differences are exact (integers); m[0..3] are the x parts
+// (R, Sx, Sy, Sxy against Tx), m[4..7] the y parts.
+template <int WIN>
+__device__ __forceinline__ void cell_moments(const Level &L, int x0, int y0, int lane, const float (&T)[WIN],
+                                             const float (&GX)[WIN], const float (&GY)[WIN], KSmem<WIN> &sm,
+                                             float (&m)[8]) {
+    constexpr int JS = KSmem<WIN>::JS;
+    const int off = stage_footprint<WIN>(L, x0, y0, lane, sm);
+    const uint8_t *jr = &sm.j[off + (lane <= WIN ? lane : WIN)];
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.f;
+    float pmv = 0.f, pdx = 0.f;
 #pragma unroll
     for (int r = 0; r <= WIN; ++r) {
-        const int row = clampi(y0 + r, 0, L.h - 1);
-        uint32_t v = 0;
-        if (ld) v = __ldg(jb + (size_t)row * L.pitch);
-        const float mv = magic_u8(v);
+        const float mv = magic_u8(jr[r * JS]);
+        const float mvr = __shfl_down_sync(kFull, mv, 1);
+        const float dx = mvr - mv;  // F(r, c+1) - F(r, c), exact
+        if (r > 0) {
+            const float e0 = T[r - 1] - (pmv - kMagic);
+            const float sy = mv - pmv;   // F10 - F00
+            const float sxy = dx - pdx;  // F11 - F10 - F01 + F00
+            const float gx = GX[r - 1], gy = GY[r - 1];
+            a[0] = fmaf(e0, gx, a[0]);
+            a[1] = fmaf(pdx, gx, a[1]);
+            a[2] = fmaf(sy, gx, a[2]);
+            a[3] = fmaf(sxy, gx, a[3]);
+            a[4] = fmaf(e0, gy, a[4]);
+            a[5] = fmaf(pdx, gy, a[5]);
+            a[6] = fmaf(sy, gy, a[6]);
+            a[7] = fmaf(sxy, gy, a[7]);
+        }
+        pmv = mv;
+        pdx = dx;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = warp_sum(a[k]);
+}
+
+// Error sweep at (qx, qy): sum |T - J_l(q + x)| over the window.
+template <int WIN>
+__device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy, int lane, const float (&T)[WIN],
+                                              KSmem<WIN> &sm) {
+    constexpr int HW = WIN / 2, JS = KSmem<WIN>::JS;
+    const float fx = floorf(qx), fy = floorf(qy);
+    const float bx = qx - fx, by = qy - fy;
+    const int off = stage_footprint<WIN>(L, (int)fx - HW, (int)fy - HW, lane, sm);
+    const uint8_t *jr = &sm.j[off + (lane <= WIN ? lane : WIN)];
+    float sa = 0.f, sb = 0.f, ph = 0.f;
+#pragma unroll
+    for (int r = 0; r <= WIN; ++r) {
+        const float mv = magic_u8(jr[r * JS]);
         const float mvr = __shfl_down_sync(kFull, mv, 1);
         const float h = fmaf(bx, mvr - mv, mv - kMagic);
         if (r > 0) {
             const float jv = fmaf(by, h - ph, ph);
-            const float res = T[r - 1] - jv;
-            if (ABS) {
-                s1 += (lane < WIN) ? fabsf(res) : 0.f;
-            } else {
-                s1 = fmaf(res, GX[r - 1], s1);
-                s2 = fmaf(res, GY[r - 1], s2);
-            }
+            const float e = (lane < WIN) ? fabsf(T[r - 1] - jv) : 0.f;
+            if (r & 1)
+                sa += e;
+            else
+                sb += e;
         }
         ph = h;
     }
-    b1 = warp_sum(s1);
-    if (!ABS) b2 = warp_sum(s2);
+    return warp_sum(sa + sb);
 }
 
 // Track one point u = (ux0, uy0) from pyramid I to pyramid J.
 template <int WIN, int GT>
 __device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
-                                            bool has_guess, float gux, float guy, int lane, KOut &o) {
+                                            bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm,
+                                            KOut &o) {
     constexpr int HW = WIN / 2;
     constexpr float N = (float)(WIN * WIN);
     constexpr float unit = grad_unit<GT>();
@@ -182,6 +272,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     o.iters = 0;
     o.tmpl = 0;
     o.errp = 0;
+    o.sweeps = 0;
     o.err = 0.f;
     o.lmin = __int_as_float(0x7fc00000);
     if (!(ux0 >= 0.f && ux0 <= (float)(I[0].w - 1) && uy0 >= 0.f && uy0 <= (float)(I[0].h - 1))) {
@@ -227,8 +318,11 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         // eta = G^-1 b in grey/px units: G = unit^2 G_s, b = unit b_s => eta = adj(G_s) b_s / (unit det_s)
         const bool fp64 = lmax > 1e5f * lmin;
         const float inv_det = (float)(1.0 / (det * (double)unit));
-        int k = 0;
-        for (; k < P.max_iters; ++k) {
+        // moments of the footprint cell last swept (valid while the integer
+        // part of q does not change)
+        int cx = INT_MIN, cy = INT_MIN;
+        float m[8];
+        for (int k = 0; k < P.max_iters; ++k) {
             const float qx = ux + gx + nux, qy = uy + gy + nuy;
             const float dist = fminf(fminf(qx + (float)HW, (float)(Jl.w - 1 + HW) - qx),
                                      fminf(qy + (float)HW, (float)(Jl.h - 1 + HW) - qy));
@@ -237,8 +331,17 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
                 o.reason = VT_LOST_OOB;
                 break;
             }
-            float b1, b2;
-            residual_pass<WIN, false>(Jl, qx, qy, lane, T, GX, GY, b1, b2);
+            const float fx = floorf(qx), fy = floorf(qy);
+            const int ix = (int)fx - HW, iy = (int)fy - HW;
+            if (ix != cx || iy != cy) {
+                cell_moments<WIN>(Jl, ix, iy, lane, T, GX, GY, sm, m);
+                cx = ix;
+                cy = iy;
+                ++o.sweeps;
+            }
+            const float bx = qx - fx, by = qy - fy, bxy = bx * by;
+            const float b1 = m[0] - bx * m[1] - by * m[2] - bxy * m[3];
+            const float b2 = m[4] - bx * m[5] - by * m[6] - bxy * m[7];
             float ex, ey;
             if (!fp64) {
                 ex = (g22 * b1 - g12 * b2) * inv_det;
@@ -275,9 +378,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             o.reason = VT_LOST_OOB;
         } else {
             // T still holds level 0's template
-            float e, unused;
-            residual_pass<WIN, true>(J[0], o.x, o.y, lane, T, GX, GY, e, unused);
-            o.err = e / N;
+            o.err = abs_residual<WIN>(J[0], o.x, o.y, lane, T, sm) / N;
             ++o.errp;
         }
     }
@@ -290,14 +391,14 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
 template <int WIN, int GT>
 __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, const KParams &P, float ux0,
                                                 float uy0, bool fb, bool has_guess, float gux, float guy, int lane,
-                                                KOut &o) {
+                                                KSmem<WIN> &sm, KOut &o) {
     const Level *A = I, *B = J;
     float x = ux0, y = uy0;
     const int npass = fb ? 2 : 1;
 #pragma unroll 1
     for (int pass = 0; pass < npass; ++pass) {
         KOut r;
-        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, r);
+        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r);
         if (pass == 0) {
             o = r;
             if (!r.status) return;
@@ -309,6 +410,7 @@ __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, 
             o.iters += r.iters;
             o.tmpl += r.tmpl;
             o.errp += r.errp;
+            o.sweeps += r.sweeps;
             if (!r.status) {
                 o.status = 0;
                 o.reason = r.reason;

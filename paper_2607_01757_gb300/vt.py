@@ -53,7 +53,7 @@ class vt_klt_params(C.Structure):
 
 
 class vt_klt_diag(C.Structure):
-    _fields_ = [("reason", vp), ("iters", vp), ("lmin", vp), ("flops", vp)]
+    _fields_ = [("reason", vp), ("iters", vp), ("lmin", vp), ("flops", vp), ("sweeps", vp)]
 
 
 def _sig(name, res, args):
@@ -245,10 +245,10 @@ class KltParams:
         return vt_klt_params(self.win, self.levels, self.max_iters, self.eps, self.min_eig, self.fb_thr)
 
 
-def _diag(reason=None, iters=None, lmin=None, flops=None):
-    if reason is None and iters is None and lmin is None and flops is None:
+def _diag(reason=None, iters=None, lmin=None, flops=None, sweeps=None):
+    if reason is None and iters is None and lmin is None and flops is None and sweeps is None:
         return None
-    return C.byref(vt_klt_diag(_ptr(reason), _ptr(iters), _ptr(lmin), _ptr(flops)))
+    return C.byref(vt_klt_diag(_ptr(reason), _ptr(iters), _ptr(lmin), _ptr(flops), _ptr(sweeps)))
 
 
 def vt_klt_track(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None, pts_guess=None, win=21,
@@ -259,20 +259,23 @@ def vt_klt_track(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None,
 
 
 def vt_klt_track_ex(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
-                    pts_guess=None, reason=None, iters=None, lmin=None, flops=None, stream=None) -> None:
+                    pts_guess=None, reason=None, iters=None, lmin=None, flops=None, sweeps=None,
+                    stream=None) -> None:
     n = int(pts_in.shape[0])
     prm = params.c()
     _check(_lib.vt_klt_track_ex(prev, cur, _ptr(pts_in), n, _ptr(pts_guess), C.byref(prm), _ptr(pts_out),
-                                _ptr(status), _ptr(err), _diag(reason, iters, lmin, flops), _stream(stream)),
+                                _ptr(status), _ptr(err), _diag(reason, iters, lmin, flops, sweeps),
+                                _stream(stream)),
            "vt_klt_track_ex")
 
 
 def vt_klt_track_fb(prev: Pyramid, cur: Pyramid, pts_in, params: KltParams, pts_out, status, err=None,
-                    reason=None, iters=None, lmin=None, flops=None, stream=None) -> None:
+                    reason=None, iters=None, lmin=None, flops=None, sweeps=None, stream=None) -> None:
     n = int(pts_in.shape[0])
     prm = params.c()
     _check(_lib.vt_klt_track_fb(prev, cur, _ptr(pts_in), n, C.byref(prm), _ptr(pts_out), _ptr(status),
-                                _ptr(err), _diag(reason, iters, lmin, flops), _stream(stream)), "vt_klt_track_fb")
+                                _ptr(err), _diag(reason, iters, lmin, flops, sweeps), _stream(stream)),
+           "vt_klt_track_fb")
 
 
 def vt_fb_check(p0, p0_back, st_f, st_b, thr, status_out, stream=None) -> None:
