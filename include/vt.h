@@ -297,6 +297,32 @@ VT_API vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr
 VT_API vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
                                int *launches_per_run);
 
+/*
+ * vt_klt_track_tasks_noalloc - the batched tracking launch for callers that
+ * cannot allocate device memory when they call: code running while a stream
+ * is captured into a CUDA graph (cudaMalloc cannot be captured), real-time
+ * loops that must not wait on the allocator or on the device-wide
+ * synchronisation cudaFree may cause, and hosts that own all device memory.
+ * The paper has no counterpart; it is an addition of this library.
+ *
+ * Tracks `ntasks` tasks (vt_track_task, pyramids already built, one gradient
+ * type, `prm` as for vt_batch_set) in one persistent launch, like the
+ * tracking launch of vt_batch_run, with the same results.  Nothing is
+ * allocated: the job table and the work counter live in a fixed array of
+ * about 22 KB in device memory that every device loading the library keeps
+ * until the process exits; the table is built on the host stack and copied
+ * with one cudaMemcpyAsync.  Limit: at most 256 tasks per call (VT_ERR_ARG
+ * beyond; any number of points per task up to 2^31 in total).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and overwrites it (the counter is reset by
+ * each call's copy), so calls that overlap on the GPU - on different streams
+ * without ordering, or from different threads - race; serialise them.
+ */
+VT_API vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int ntasks, const vt_klt_params *prm,
+                                            void *cuda_stream);
+
 /* Human-readable name of a status code. */
 VT_API const char *vt_status_str(vt_status s);
 

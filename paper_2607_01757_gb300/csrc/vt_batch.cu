@@ -431,3 +431,127 @@ vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_pe
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tracking of many tasks without any allocation.
+//
+// Some callers cannot allocate device memory at call time: code that runs
+// while a stream is being captured into a CUDA graph (cudaMalloc is not a
+// capturable operation), real-time loops that must not block on the
+// allocator or on the implicit device synchronisation cudaFree can cause,
+// and hosts that hand out all device memory themselves.  For them the tracking
+// launch of vt_batch can run with its job table and work counter in the
+// file-scope array below instead of a vt_batch's allocations.
+namespace vt {
+
+constexpr int kNoAllocMaxTasks = 256;
+constexpr size_t kNoAllocTaskOff = 256;  // after a BatchHdr (checked below)
+constexpr size_t kNoAllocPrefixOff = kNoAllocTaskOff + sizeof(BTask) * kNoAllocMaxTasks;
+constexpr size_t kNoAllocCounterOff = (kNoAllocPrefixOff + sizeof(int) * kNoAllocMaxTasks + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocCounterOff + 256;
+static_assert(sizeof(BatchHdr) <= kNoAllocTaskOff, "header must fit before the task table");
+
+// Shared by every call on a device; kept until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static uint8_t *g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device (looked up on
+// the first call per device; the array's host-side name is not an address).
+static vt_status noalloc_scratch(uint8_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return VT_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = (uint8_t *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return VT_OK;
+}
+
+}  // namespace vt
+
+extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int ntasks, const vt_klt_params *prm,
+                                                void *cuda_stream) {
+    if (!prm || ntasks < 0 || (ntasks > 0 && !tasks)) return VT_ERR_ARG;
+    if (ntasks > kNoAllocMaxTasks) return VT_ERR_ARG;  // beyond the fixed table
+    if (!window_supported(prm->win) || prm->levels < 0 || prm->levels > VT_MAX_LEVELS || prm->max_iters < 1 ||
+        !(prm->eps >= 0.f) || !(prm->min_eig >= 0.f) || !(prm->fb_thr >= 0.f))
+        return VT_ERR_ARG;
+    if (ntasks == 0) return VT_OK;
+    const int gtype = tasks[0].prev ? tasks[0].prev->gtype : VT_GRAD_NONE;
+    if (gtype != VT_GRAD_S16 && gtype != VT_GRAD_F16) return VT_ERR_ARG;
+    long total = 0;
+    for (int t = 0; t < ntasks; ++t) {
+        const vt_track_task &tk = tasks[t];
+        if (!tk.prev || !tk.cur || tk.n < 0 || (tk.n > 0 && (!tk.pts_in || !tk.pts_out || !tk.status)))
+            return VT_ERR_ARG;
+        const int L = tk.levels > 0 ? tk.levels : prm->levels;
+        if (tk.levels < 0 || L < 1 || L > tk.prev->levels || L > tk.cur->levels) return VT_ERR_ARG;
+        if (tk.prev->gtype != gtype || (tk.fb && tk.cur->gtype != gtype)) return VT_ERR_ARG;
+        total += tk.n;
+    }
+    if (total > 0x7fffffff) return VT_ERR_ARG;
+    if (total == 0) return VT_OK;
+    uint8_t *dev = nullptr;
+    vt_status st = noalloc_scratch(&dev);
+    if (st != VT_OK) return st;
+    // job table built on the host stack, copied into the scratch array with
+    // the work counter zeroed in the same copy
+    alignas(16) uint8_t host[kNoAllocCounterOff + sizeof(int)];
+    memset(host, 0, sizeof(host));
+    BatchHdr *H = reinterpret_cast<BatchHdr *>(host);
+    H->ntasks = ntasks;
+    H->total_points = (int)total;
+    H->off_tasks = (int)kNoAllocTaskOff;
+    H->off_prefix = (int)kNoAllocPrefixOff;
+    H->P.win = prm->win;
+    H->P.levels = prm->levels;
+    H->P.max_iters = prm->max_iters;
+    H->P.eps2 = prm->eps * prm->eps;
+    H->P.min_eig = prm->min_eig;
+    H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
+    BTask *bt = reinterpret_cast<BTask *>(host + kNoAllocTaskOff);
+    int *p0s = reinterpret_cast<int *>(host + kNoAllocPrefixOff);
+    int p0 = 0;
+    for (int t = 0; t < ntasks; ++t) {
+        const vt_track_task &tk = tasks[t];
+        bt[t].I = tk.prev->dev_lv;
+        bt[t].J = tk.cur->dev_lv;
+        bt[t].pts_in = reinterpret_cast<const float2 *>(tk.pts_in);
+        bt[t].pts_out = reinterpret_cast<float2 *>(tk.pts_out);
+        bt[t].status = tk.status;
+        bt[t].err = tk.err;
+        bt[t].reason = tk.reason;
+        bt[t].flops = tk.flops;
+        bt[t].n = tk.n;
+        bt[t].fb = tk.fb ? 1 : 0;
+        bt[t].levels = tk.levels > 0 ? tk.levels : prm->levels;
+        bt[t].p0 = p0;
+        p0s[t] = p0;
+        p0 += tk.n;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (cudaMemcpyAsync(dev, host, sizeof(host), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    const KltBatchKernel kb = klt_batch_kernel(prm->win, gtype, 4);
+    if (!kb.fn) return VT_ERR_ARG;
+    int sms = 0, occ = 0, d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)kb.fn, 4 * 32, kb.smem);
+    if (sms < 1) sms = 1;
+    if (occ < 1) occ = 1;
+    kb.fn<<<sms * occ, 4 * 32, kb.smem, s>>>(dev, reinterpret_cast<int *>(dev + kNoAllocCounterOff));
+    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+}

@@ -397,3 +397,15 @@ def vt_batch_info(b: Batch):
     g, w, pg, nl = i32(), i32(), i32(), i32()
     _check(_lib.vt_batch_info(b, C.byref(g), C.byref(w), C.byref(pg), C.byref(nl)), "vt_batch_info")
     return dict(klt_grid=g.value, klt_warps=w.value, pyr_grid=pg.value, launches_per_run=nl.value)
+
+
+_sig("vt_klt_track_tasks_noalloc", i32, [C.POINTER(vt_track_task), i32, C.POINTER(vt_klt_params), vp])
+
+
+def vt_klt_track_tasks_noalloc(tasks, params: KltParams, stream=None) -> None:
+    """Track every task of `tasks` (vt_track_task list) in one launch that
+    allocates no device memory (see include/vt.h)."""
+    ta = (vt_track_task * max(1, len(tasks)))(*tasks)
+    prm = params.c()
+    _check(_lib.vt_klt_track_tasks_noalloc(ta, len(tasks), C.byref(prm), _stream(stream)),
+           "vt_klt_track_tasks_noalloc")
