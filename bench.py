@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="4 streams, for profiler captures")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-streams", type=int, default=64)
+    ap.add_argument("--served-requests", type=int, default=10000)
+    ap.add_argument("--served-budget-gb", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -138,6 +142,9 @@ def run_native(a, rank, world, local_rank):
     import numpy as np
 
     specs, frames = make_workload(a.streams, a.frames, a.seed + 1000 * rank, os.cpu_count() or 1)
+    served_wl = None
+    if not a.no_served:
+        served_wl = make_workload(a.served_streams, a.frames, a.seed + 1 + 1000 * rank, os.cpu_count() or 1)
 
     import torch
 
@@ -404,6 +411,11 @@ def run_native(a, rank, world, local_rank):
                "h2d_bytes_per_step": h2d["b"] // a.steps, "d2h_bytes_per_step": d2h["b"] // a.steps,
                "p50_ms": float(np.percentile(ems, 50)), "p99_ms": float(np.percentile(ems, 99))}
 
+    # ---------------- served (request loop, continuous batching) ----------------
+    served = None
+    if served_wl is not None:
+        served = run_served(a, served_wl, prm, barrier, max_over_ranks, sum_over_ranks)
+
     # ---------------- CPU baseline (oracle), rank 0 at N = 1 only -------------
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -451,6 +463,7 @@ def run_native(a, rank, world, local_rank):
                              / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": None,
                              "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src},
+        "served": served,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -458,6 +471,61 @@ def run_native(a, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def run_served(a, wl, prm, barrier, max_over_ranks, sum_over_ranks):
+    """Request loop over the served stream mix: a seeded real-time trace
+    (20-30 Hz per stream, exponential jitter), continuous batching with an
+    HBM admission budget, then the same trace served one request at a time
+    with single-pair calls, and a run with a budget of a quarter of the
+    streams' total footprint to exercise admission."""
+    from paper_2607_01757_gb300.server import Server, make_trace
+
+    specs, frames = wl
+    out = {"workload": f"{len(specs)} streams of the stream mix at 20-30 Hz (exponential jitter), "
+                       f"{a.served_requests} frame-pair requests, FB-checked temporal + stereo tracking, "
+                       f"host frames in, host results out",
+           "budget_gb": a.served_budget_gb}
+    srv = Server(specs, frames, prm, budget_bytes=int(a.served_budget_gb * (1 << 30)))
+    warm = make_trace(specs, 2 * len(specs), seed=a.seed + 77, frames_per_stream=a.frames)
+    srv.serve(warm, realtime=False)  # graph capture and first-touch outside the measurement
+    srv.free()
+    srv = Server(specs, frames, prm, budget_bytes=int(a.served_budget_gb * (1 << 30)))
+    trace = make_trace(specs, a.served_requests, seed=a.seed + 5, frames_per_stream=a.frames)
+    barrier()
+    st = srv.serve(trace, realtime=True).summary()
+    barrier()
+    st["features_per_s"] = sum_over_ranks(st["features_per_s"])
+    out["batched"] = st
+    srv.free()
+    srv = Server(specs, frames, prm, budget_bytes=int(a.served_budget_gb * (1 << 30)))
+    trace = make_trace(specs, a.served_requests, seed=a.seed + 5, frames_per_stream=a.frames)
+    barrier()
+    sp = srv.serve_plain(trace, realtime=True).summary()
+    barrier()
+    sp["features_per_s"] = sum_over_ranks(sp["features_per_s"])
+    out["plain"] = sp
+    # capacity: the same requests all available at once (no arrival pacing)
+    for name, fn in (("batched_saturated", "serve"), ("plain_saturated", "serve_plain")):
+        srv.free()
+        srv = Server(specs, frames, prm, budget_bytes=int(a.served_budget_gb * (1 << 30)))
+        trace = make_trace(specs, a.served_requests, seed=a.seed + 5, frames_per_stream=a.frames)
+        barrier()
+        sx = getattr(srv, fn)(trace, realtime=False).summary()
+        barrier()
+        sx["features_per_s"] = sum_over_ranks(sx["features_per_s"])
+        out[name] = sx
+    tight = sum(srv.footprint) // 4
+    srv.free()
+    srv = Server(specs, frames, prm, budget_bytes=tight)
+    per = max(3, a.served_requests // (4 * len(specs)))
+    trace = make_trace(specs, min(a.served_requests, per * len(specs)), seed=a.seed + 6,
+                       frames_per_stream=a.frames, session=per)
+    sb = srv.serve(trace, realtime=True).summary()
+    sb["budget_bytes"] = tight
+    out["batched_quarter_budget"] = sb
+    srv.free()
+    return out
 
 
 def cpu_baseline(specs, frames, prm, seconds):

@@ -404,6 +404,7 @@ static vt_status alloc_pyramid(int w, int h, int levels, vt_pyramid **out) {
         grad_off[l] = off;
         off += ((size_t)p->lv[l].gpitch * 4 * p->lv[l].h + 255) / 256 * 256;
     }
+    off += 256;  // slack: wide loads of a footprint may read a few bytes past a row end
     if (cudaMalloc(&p->base, off) != cudaSuccess) {
         cudaGetLastError();
         free(p);

@@ -67,7 +67,8 @@ class BatchedTracker:
             s.out_s = mk() if sp.stereo else ()
             self.streams.append(s)
         nf = sum(2 if s.stereo else 1 for s in self.streams)
-        self.batch = vt.Batch(max(1, nf), max(1, nf))
+        self.batch_capacity = (max(1, nf), max(1, nf))
+        self.batch = vt.Batch(*self.batch_capacity)
         self._flops = None
 
     # ------------------------------------------------------------ descriptors

@@ -31,6 +31,9 @@ class VTError(RuntimeError):
 
 
 def _load() -> C.CDLL:
+    override = os.environ.get("VT_LIBRARY")
+    if override:  # an explicitly chosen build of libvt.so
+        return C.CDLL(override)
     path = _build.LIB
     if not os.path.exists(path) or _build.needs_build():
         try:
