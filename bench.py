@@ -459,7 +459,7 @@ def run_native(a, rank, world, local_rank):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "flops_per_launch": klt_flops, "launch_ms": klt_avg_s * 1e3,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
-        "roofline_pyramid": {"bound": "hbm", "kernel": "k_pyr_batch+k_scharr_batch", "achieved": pyr_bytes / pyr_avg_s
+        "roofline_pyramid": {"bound": "hbm", "kernel": "k_pyr_batch+k_pyr_tail", "achieved": pyr_bytes / pyr_avg_s
                              / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": None,
                              "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src},

@@ -123,6 +123,7 @@ struct vt_batch {
     int klt_warps;        // warps per CTA of the KLT launch (4 or 8)
     int klt_ctas_per_sm;  // 0 = occupancy limit
     int pyr_grid;
+    int tail_grid;  // CTAs of the tail launch (one frame each at a time)
 };
 
 namespace vt {
@@ -134,7 +135,8 @@ static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks,
     off_frames = (int)o;
     o = align_up(o + sizeof(BFrame) * F, 64);
     off_jobs = (int)o;
-    o = align_up(o + sizeof(BLvlJob) * (size_t)F * VT_MAX_LEVELS, 64);
+    // VT_MAX_LEVELS - 1 tiled lists of F jobs, then the tail list of up to 8 bands per frame
+    o = align_up(o + sizeof(BLvlJob) * (size_t)F * (VT_MAX_LEVELS - 1 + 8), 64);
     off_tasks = (int)o;
     o = align_up(o + sizeof(BTask) * T, 64);
     off_prefix = (int)o;
@@ -159,7 +161,7 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
         return VT_ERR_CUDA;
     }
     if (ev && ev[0]) cudaEventRecord(ev[0], s);
-    vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, tp.pyr_grid, s);
+    vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, b->tail_grid, s);
     if (st != VT_OK) return st;
     if (ev && ev[1]) cudaEventRecord(ev[1], s);
     const KltBatchKernel kb = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
@@ -200,6 +202,7 @@ vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out) {
     }
     b->klt_warps = 4;
     b->klt_ctas_per_sm = 0;
+    b->tail_grid = 8 * b->cap_frames < 2 * b->sms ? 8 * b->cap_frames : 2 * b->sms;
     b->pyr_grid = b->sms * (pyr_batch_blocks_per_sm() > 0 ? pyr_batch_blocks_per_sm() : 1);
     b->staged = -1;
     *out = b;
@@ -283,7 +286,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
     BFrame *bf = reinterpret_cast<BFrame *>(tab + H->off_frames);
     BLvlJob *jobs = reinterpret_cast<BLvlJob *>(tab + H->off_jobs);
-    int maxL = 1;
+    int maxL = 1, maxC = 0;
     for (int f = 0; f < nframes; ++f) {
         const vt_frame_job &fj = frames[f];
         vt_pyramid *p = fj.pyr;
@@ -294,24 +297,36 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
         bf[f].levels = p->levels;
         p->gtype = (int)gtype;
         if (p->levels > maxL) maxL = p->levels;
+        const int c = tail_start_level(p);
+        if (c > maxC) maxC = c;
     }
     for (int l = 0; l < VT_MAX_LEVELS; ++l) {
         BLvlJob *lj = jobs + (size_t)l * b->cap_frames;
         int nj = 0, tiles = 0;
         for (int f = 0; f < nframes; ++f) {
             const vt_pyramid *p = frames[f].pyr;
-            int tx, nt;
+            const int c = tail_start_level(p);
             if (l < VT_MAX_LEVELS - 1) {
-                if (p->levels <= l + 1) continue;
-                nt = pyr_tiles(p->lv[l].w, p->lv[l].h, tx);
+                if (l >= c) continue;  // levels from c on are built by the tail kernel
+                int tx = 0;
+                const int nt = pyr_tiles(p->lv[l].w, p->lv[l].h, tx);
+                lj[nj].frame = f;
+                lj[nj].tiles_x = tx;
+                lj[nj].tile0 = tiles;
+                lj[nj].aux = c;
+                tiles += nt;
+                ++nj;
             } else {
-                nt = scharr_tiles(p->lv[p->levels - 1].w, p->lv[p->levels - 1].h, tx);
+                const int parts = tail_parts(p);
+                for (int q = 0; q < parts; ++q) {
+                    lj[nj].frame = f;
+                    lj[nj].tiles_x = q;
+                    lj[nj].tile0 = parts;
+                    lj[nj].aux = c;
+                    ++nj;
+                    ++tiles;
+                }
             }
-            lj[nj].frame = f;
-            lj[nj].tiles_x = tx;
-            lj[nj].tile0 = tiles;
-            tiles += nt;
-            ++nj;
         }
         H->njobs[l] = nj;
         H->ntiles[l] = tiles;
@@ -340,7 +355,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     H->total_points = (int)total;
     H->maxL = maxL;
     Topo &tp = b->topo[k];
-    tp.maxL = maxL;
+    tp.maxL = maxC;  // tiled pyramid launches of this run
     tp.gtype = (int)gtype;
     tp.win = prm->win;
     tp.klt_warps = b->klt_warps;
@@ -426,7 +441,7 @@ vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_pe
     if (klt_grid_ctas) *klt_grid_ctas = b->topo[k].klt_grid;
     if (klt_warps_per_cta) *klt_warps_per_cta = b->topo[k].klt_warps;
     if (pyr_grid_ctas) *pyr_grid_ctas = b->topo[k].pyr_grid;
-    if (launches_per_run) *launches_per_run = b->staged >= 0 ? (b->topo[k].maxL - 1) + 1 + 1 : 0;
+    if (launches_per_run) *launches_per_run = b->staged >= 0 ? b->topo[k].maxL + 1 + 1 : 0;
     return VT_OK;
 }
 

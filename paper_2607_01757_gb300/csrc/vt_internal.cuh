@@ -107,8 +107,13 @@ struct BLvlJob {
     int frame;
     int tiles_x;
     int tile0;  // first tile of this job within its launch
-    int pad;
+    int aux;    // tail list: first level the tail kernel builds (c); in tail
+                // lists tiles_x is the band index and tile0 the band count
 };
+
+// Levels of at most this many pixels are built by the tail kernel, one CTA
+// per frame, entirely in shared memory.
+constexpr int kTailMaxPx = 40960;
 
 struct BTask {
     const Level *I;  // template pyramid (device level table)
@@ -124,7 +129,7 @@ struct BTask {
 
 struct BatchHdr {
     int nframes, ntasks, total_points, maxL;
-    int njobs[VT_MAX_LEVELS];   // [l < VT_MAX_LEVELS-1]: pyramid launch l; [VT_MAX_LEVELS-1]: last-level Scharr
+    int njobs[VT_MAX_LEVELS];   // [l < VT_MAX_LEVELS-1]: tiled pyramid launch l; [VT_MAX_LEVELS-1]: tail jobs
     int ntiles[VT_MAX_LEVELS];
     int cap_frames, cap_tasks;
     int off_frames, off_jobs, off_tasks, off_prefix;
@@ -132,10 +137,13 @@ struct BatchHdr {
 };
 
 // Host helpers implemented in vt_pyramid.cu.
-vt_status launch_pyr_batch(const uint8_t *dev_tab, int maxL, int gtype, int grid_pyr, int grid_sc, cudaStream_t s);
+vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,
+                           cudaStream_t s);
+int tail_start_level(const vt_pyramid *p);
+int tail_parts(const vt_pyramid *p);
 int pyr_batch_blocks_per_sm();
 int pyr_tiles(int w, int h, int &tiles_x);
-int scharr_tiles(int w, int h, int &tiles_x);
+__host__ __device__ int scharr_tiles(int w, int h, int &tiles_x);
 bool window_supported(int win);
 vt_status launch_pyrdown(const PyrJobs &jobs, int total_blocks, int gtype, cudaStream_t s);
 vt_status launch_scharr(const GradJobs &jobs, int total_blocks, int gtype, cudaStream_t s);

@@ -26,7 +26,7 @@ constexpr int PD_TW = 64;              // output tile width (level l+1)
 constexpr int PD_TH = 16;              // output tile height
 constexpr int PD_IW = 2 * PD_TW + 32;  // staged bytes per row (16-byte chunks)
 constexpr int PD_IH = 2 * PD_TH + 3;   // staged rows
-constexpr int PD_VW = 2 * PD_TW + 4;   // vertical-pass columns
+constexpr int PD_VW = 2 * PD_TW + 8;   // vertical-pass columns (staged columns 12 .. 12 + PD_VW)
 constexpr int PD_THREADS = 256;
 
 constexpr int SC_TW = 64;
@@ -99,65 +99,128 @@ __device__ __forceinline__ void copy_out(const uint8_t (*s)[IW], int r0, int c0,
 // One output tile (tx, ty) of the pyramid step src -> dst; with GRAD also the
 // Scharr planes of src over the matching 2*TW x 2*TH region, and with `copy`
 // a copy of that src region (level 0 of a pyramid built from a caller image).
+// Needs blockDim.x == PD_THREADS.
+//
+// The staged tile holds image columns ix0 .. ix0 + PD_IW with ix0 = 2*ox0 - 16
+// and rows iy0 .. iy0 + PD_IH with iy0 = 2*oy0 - 2.
+//  * vertical [1 4 6 4 1] pass on 32-bit words: the even and odd bytes of a
+//    word are summed as two packed 16-bit lanes (at most 16 * 255 = 4080, no
+//    carry between lanes), 4 columns per operation;
+//  * horizontal pass: 4 outputs per thread from 6 packed column pairs;
+//  * Scharr: each thread owns 4 columns x 4 rows and slides a 3-row window of
+//    6 bytes per row (3 aligned word loads per row), with the separable form
+//    dx = s(x+1) - s(x-1), s = 3 top + 10 mid + 3 bottom, and
+//    dy = 3 d(x-1) + 10 d(x) + 3 d(x+1), d = bottom - top.
+template <bool GRAD, int GT>
+__device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int dpitch, uint32_t *grad, int gpitch,
+                                                 uint8_t *copy, int cpitch, int tx, int ty,
+                                                 uint8_t (*s_in)[PD_IW], uint16_t (*s_v)[PD_VW]);
+
 template <bool GRAD, int GT>
 __device__ __forceinline__ void pyr_tile(const uint8_t *src, int w, int h, int spitch, bool vec_ok, uint8_t *dst,
                                          int dpitch, uint32_t *grad, int gpitch, uint8_t *copy, int cpitch, int tx,
                                          int ty, uint8_t (*s_in)[PD_IW], uint16_t (*s_v)[PD_VW]) {
+    stage_tile<PD_IH, PD_IW>(s_in, src, w, h, spitch, 2 * tx * PD_TW - 16, 2 * ty * PD_TH - 2, vec_ok);
+    __syncthreads();
+    pyr_tile_compute<GRAD, GT>(w, h, dst, dpitch, grad, gpitch, copy, cpitch, tx, ty, s_in, s_v);
+}
+
+// The computing part of pyr_tile on an already staged tile.
+template <bool GRAD, int GT>
+__device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int dpitch, uint32_t *grad, int gpitch,
+                                                 uint8_t *copy, int cpitch, int tx, int ty,
+                                                 uint8_t (*s_in)[PD_IW], uint16_t (*s_v)[PD_VW]) {
     const int W = (w + 1) >> 1, H = (h + 1) >> 1;
     const int ox0 = tx * PD_TW, oy0 = ty * PD_TH;
-    const int ix0 = 2 * ox0 - 16, iy0 = 2 * oy0 - 2;
 
-    stage_tile<PD_IH, PD_IW>(s_in, src, w, h, spitch, ix0, iy0, vec_ok);
-    __syncthreads();
-
-    // vertical pass: s_v[r][c] for input column 2*ox0 - 2 + c (staged column c + 14)
-    for (int i = threadIdx.x; i < PD_TH * PD_VW; i += blockDim.x) {
-        const int r = i / PD_VW, c = i - r * PD_VW;
-        const int cc = c + 14;
-        s_v[r][c] = (uint16_t)(s_in[2 * r][cc] + 4 * s_in[2 * r + 1][cc] + 6 * s_in[2 * r + 2][cc] +
-                               4 * s_in[2 * r + 3][cc] + s_in[2 * r + 4][cc]);
+    // vertical pass: s_v[r][c] = sum_k [1 4 6 4 1]_k staged(2r + k, 12 + c)
+    for (int i = threadIdx.x; i < PD_TH * (PD_VW / 4); i += PD_THREADS) {
+        const int r = i / (PD_VW / 4), j = i - r * (PD_VW / 4);
+        uint32_t lo[5], hi[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const uint32_t v = *reinterpret_cast<const uint32_t *>(&s_in[2 * r + k][12 + 4 * j]);
+            lo[k] = v & 0x00FF00FFu;
+            hi[k] = (v >> 8) & 0x00FF00FFu;
+        }
+        const uint32_t sl = lo[0] + lo[4] + 4u * (lo[1] + lo[3]) + 6u * lo[2];
+        const uint32_t sh = hi[0] + hi[4] + 4u * (hi[1] + hi[3]) + 6u * hi[2];
+        uint32_t *out = reinterpret_cast<uint32_t *>(&s_v[r][0]) + 2 * j;
+        *reinterpret_cast<uint2 *>(out) = make_uint2(__byte_perm(sl, sh, 0x5410), __byte_perm(sl, sh, 0x7632));
     }
     if (GRAD) {
-        // gradients of the source level over [2*ox0, 2*ox0 + 2*TW) x [2*oy0, 2*oy0 + 2*TH)
-        constexpr int GW = 2 * PD_TW, GH = 2 * PD_TH;
-        for (int i = threadIdx.x; i < GH * (GW / 4); i += blockDim.x) {
-            const int r = i / (GW / 4), x4 = (i - r * (GW / 4)) * 4;
-            const int y = 2 * oy0 + r, x = 2 * ox0 + x4;
-            if (y >= h || x >= w) continue;
-            uint32_t g[4];
+        const int g = threadIdx.x & 31, rg = threadIdx.x >> 5;
+        const int xr = 4 * g, x = 2 * ox0 + xr;
+        int t0[6], t1[6], t2[6];
+        auto load_row = [&](int sr, int (&v)[6]) {
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(&s_in[sr][12 + xr]);
+            const uint32_t a = wp[0], b = wp[1], c = wp[2];
+            v[0] = (int)(a >> 24);
+            v[1] = (int)(b & 0xffu);
+            v[2] = (int)((b >> 8) & 0xffu);
+            v[3] = (int)((b >> 16) & 0xffu);
+            v[4] = (int)(b >> 24);
+            v[5] = (int)(c & 0xffu);
+        };
+        load_row(4 * rg + 1, t0);
+        load_row(4 * rg + 2, t1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int dx, dy;
-                scharr_at<PD_IW>(s_in, r + 2, x4 + q + 16, dx, dy);
-                g[q] = pack_grad<GT>(dx, dy);
+        for (int i = 0; i < 4; ++i) {
+            load_row(4 * rg + 3 + i, t2);
+            const int y = 2 * oy0 + 4 * rg + i;
+            if (y < h && x < w) {
+                int sm[6], dd[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    sm[k] = 3 * (t0[k] + t2[k]) + 10 * t1[k];
+                    dd[k] = t2[k] - t0[k];
+                }
+                uint32_t gq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    gq[q] = pack_grad<GT>(sm[q + 2] - sm[q], 3 * (dd[q] + dd[q + 2]) + 10 * dd[q + 1]);
+                uint32_t *d = grad + (size_t)y * gpitch + x;
+                if (x + 3 < w) {
+                    *reinterpret_cast<uint4 *>(d) = make_uint4(gq[0], gq[1], gq[2], gq[3]);
+                } else {
+                    for (int q = 0; q < 4 && x + q < w; ++q) d[q] = gq[q];
+                }
             }
-            uint32_t *d = grad + (size_t)y * gpitch + x;
-            if (x + 3 < w) {
-                *reinterpret_cast<uint4 *>(d) = make_uint4(g[0], g[1], g[2], g[3]);
-            } else {
-                for (int q = 0; q < 4 && x + q < w; ++q) d[q] = g[q];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                t0[k] = t1[k];
+                t1[k] = t2[k];
             }
         }
     }
     if (copy) copy_out<PD_IW>(s_in, 2, 16, 2 * PD_TH, copy, cpitch, 2 * ox0, 2 * oy0, w, h);
     __syncthreads();
-    // horizontal pass: 4 consecutive outputs per thread
-    for (int i = threadIdx.x; i < PD_TH * (PD_TW / 4); i += blockDim.x) {
-        const int r = i / (PD_TW / 4), x4 = (i - r * (PD_TW / 4)) * 4;
+    // horizontal pass: 4 consecutive outputs per thread; output x uses
+    // s_v columns 2x + 2 .. 2x + 6
+    {
+        const int r = threadIdx.x >> 4, x4 = (threadIdx.x & 15) * 4;
         const int oy = oy0 + r, ox = ox0 + x4;
-        if (oy >= H || ox >= W) continue;
-        const uint16_t *v = &s_v[r][2 * x4];
-        uint32_t o[4];
+        if (oy < H && ox < W) {
+            const uint32_t *pr = reinterpret_cast<const uint32_t *>(&s_v[r][0]) + x4 + 1;
+            uint32_t v[12];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t s = v[2 * q] + 4u * v[2 * q + 1] + 6u * v[2 * q + 2] + 4u * v[2 * q + 3] + v[2 * q + 4];
-            o[q] = (s + 128u) >> 8;
-        }
-        uint8_t *d = dst + (size_t)oy * dpitch + ox;
-        if (ox + 3 < W) {
-            *reinterpret_cast<uint32_t *>(d) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
-        } else {
-            for (int q = 0; q < 4 && ox + q < W; ++q) d[q] = (uint8_t)o[q];
+            for (int k = 0; k < 6; ++k) {
+                const uint32_t pk = pr[k];
+                v[2 * k] = pk & 0xffffu;
+                v[2 * k + 1] = pk >> 16;
+            }
+            uint32_t o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t sum = v[2 * q] + v[2 * q + 4] + 4u * (v[2 * q + 1] + v[2 * q + 3]) + 6u * v[2 * q + 2];
+                o[q] = (sum + 128u) >> 8;
+            }
+            uint8_t *d = dst + (size_t)oy * dpitch + ox;
+            if (ox + 3 < W) {
+                *reinterpret_cast<uint32_t *>(d) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+            } else {
+                for (int q = 0; q < 4 && ox + q < W; ++q) d[q] = (uint8_t)o[q];
+            }
         }
     }
 }
@@ -242,54 +305,211 @@ __device__ __forceinline__ int find_job(const BLvlJob *jobs, int n, int t) {
 }
 
 // Launch `l` (< VT_MAX_LEVELS - 1): level l -> l+1 plus the Scharr planes of
-// level l for every frame of the batch that has level l+1.  Level 0 reads the
-// caller's image and writes the pyramid's level-0 copy from the same tile.
+// level l for every frame of the batch whose tail starts above l.  Level 0
+// reads the caller's image and writes the pyramid's level-0 copy from the
+// same tile.  The job list is first copied to shared memory so the per-tile
+// job search does not chain global loads.
+constexpr int kJobsInSmem = 256;
+
+struct PyrTileRef {
+    const uint8_t *src;
+    int w, h, pitch;
+    bool vec_ok;
+    int ix0, iy0;
+};
+
 template <int GT>
 __global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l) {
     __shared__ __align__(16) uint8_t s_in[PD_IH][PD_IW];
     __shared__ uint16_t s_v[PD_TH][PD_VW];
+    __shared__ BLvlJob s_jobs[kJobsInSmem];
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const int njobs = H->njobs[l], tiles = H->ntiles[l];
+    if ((int)blockIdx.x >= tiles) return;
     const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
-    const BLvlJob *jobs = reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)l * H->cap_frames;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const BLvlJob *gjobs = reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)l * H->cap_frames;
+    const bool in_smem = njobs <= kJobsInSmem;
+    if (in_smem) {
+        for (int i = threadIdx.x; i < njobs; i += blockDim.x) s_jobs[i] = gjobs[i];
+        __syncthreads();
+    }
+    const BLvlJob *jobs = in_smem ? s_jobs : gjobs;
+    // where tile t's input lives, and its frame and tile coordinates
+    auto locate = [&](int t, PyrTileRef &r, BFrame &fr, int &tx, int &ty) {
         const BLvlJob jb = jobs[find_job(jobs, njobs, t)];
-        const BFrame fr = frames[jb.frame];
-        const Level src = fr.lv[l], dst = fr.lv[l + 1];
+        fr = frames[jb.frame];
+        const Level src = fr.lv[l];
         const int tt = t - jb.tile0;
-        const int ty = tt / jb.tiles_x, tx = tt - ty * jb.tiles_x;
-        if (l == 0)
-            pyr_tile<true, GT>(fr.img, src.w, src.h, fr.pitch, fr.vec_ok, dst.img, dst.pitch, src.grad, src.gpitch,
-                               src.img, src.pitch, tx, ty, s_in, s_v);
-        else
-            pyr_tile<true, GT>(src.img, src.w, src.h, src.pitch, true, dst.img, dst.pitch, src.grad, src.gpitch,
-                               nullptr, 0, tx, ty, s_in, s_v);
+        ty = tt / jb.tiles_x;
+        tx = tt - ty * jb.tiles_x;
+        r.src = l == 0 ? fr.img : src.img;
+        r.pitch = l == 0 ? fr.pitch : src.pitch;
+        r.vec_ok = l == 0 ? fr.vec_ok != 0 : true;
+        r.w = src.w;
+        r.h = src.h;
+        r.ix0 = 2 * tx * PD_TW - 16;
+        r.iy0 = 2 * ty * PD_TH - 2;
+    };
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        PyrTileRef r;
+        BFrame fr;
+        int tx, ty;
+        locate(t, r, fr, tx, ty);
+        const Level src = fr.lv[l], dst = fr.lv[l + 1];
+        pyr_tile<true, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad, src.gpitch,
+                           l == 0 ? src.img : nullptr, src.pitch, tx, ty, s_in, s_v);
         __syncthreads();
     }
 }
 
-// Scharr planes of each frame's last level (which no pyramid step covers);
-// a one-level pyramid also gets its level-0 copy here.
+// ------------------------------------------------------------------ tail
+constexpr int TAIL_THREADS = 1024;
+constexpr int TAIL_A = kTailMaxPx;             // level c (<= kTailMaxPx pixels)
+constexpr int TAIL_B = kTailMaxPx / 2 + 512;   // level c+1 (<= (w h + w + h + 1) / 4 pixels)
+constexpr int TAIL_SMEM = TAIL_A + TAIL_B;
+
+// First level the tail kernel builds: the first whose rows (at the
+// pyramid's pitch) fit in kTailMaxPx bytes, or the last.
+int tail_start_level(const vt_pyramid *p) {
+    for (int l = 0; l < p->levels; ++l)
+        if ((long)p->lv[l].pitch * p->lv[l].h <= kTailMaxPx) return l;
+    return p->levels - 1;
+}
+
+// Row bands (CTAs) of a frame's tail: about 4096 pixels of level c each, at most 8.
+int tail_parts(const vt_pyramid *p) {
+    const int c = tail_start_level(p);
+    const long px = (long)p->lv[c].w * p->lv[c].h;
+    if ((long)p->lv[c].pitch * p->lv[c].h > kTailMaxPx) return 1;
+    int n = (int)((px + 4095) / 4096);
+    n = n < 1 ? 1 : (n > 8 ? 8 : n);
+    return n < p->lv[c].h ? n : (p->lv[c].h > 0 ? p->lv[c].h : 1);
+}
+
+// Reflect-101 neighbours one step away (valid for any n >= 1).
+__device__ __forceinline__ int refl_m1(int i, int n) { return i > 0 ? i - 1 : (n > 1 ? 1 : 0); }
+__device__ __forceinline__ int refl_p1(int i, int n) { return i < n - 1 ? i + 1 : (n > 1 ? n - 2 : 0); }
+
+// Scharr of rows [y0, y1) of a w x h level held in shared memory; warps take
+// rows, lanes take columns.
 template <int GT>
-__global__ void __launch_bounds__(SC_THREADS) k_scharr_batch(const uint8_t *tab) {
-    __shared__ __align__(16) uint8_t s_in[SC_IH][SC_IW];
+__device__ __forceinline__ void tail_scharr(const uint8_t *s, int stride, int w, int h, int y0, int y1,
+                                            uint32_t *grad, int gpitch) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int y = y0 + (threadIdx.x >> 5); y < y1; y += nw) {
+        const uint8_t *rm = s + refl_m1(y, h) * stride, *r0 = s + y * stride, *rp = s + refl_p1(y, h) * stride;
+        uint32_t *g = grad + (size_t)y * gpitch;
+        for (int x = lane; x < w; x += 32) {
+            const int xm = refl_m1(x, w), xp = refl_p1(x, w);
+            const int a00 = rm[xm], a01 = rm[x], a02 = rm[xp];
+            const int a10 = r0[xm], a12 = r0[xp];
+            const int a20 = rp[xm], a21 = rp[x], a22 = rp[xp];
+            const int sm = 3 * (a02 - a00) + 10 * (a12 - a10) + 3 * (a22 - a20);
+            const int dy = 3 * (a20 - a00) + 10 * (a21 - a01) + 3 * (a22 - a02);
+            g[x] = pack_grad<GT>(sm, dy);
+        }
+    }
+}
+
+// pyrDown of a w x h level in shared memory (row stride `stride`) into d
+// (shared, tight rows) and g (global).
+__device__ __forceinline__ void tail_pyrdown(const uint8_t *s, int stride, int w, int h, uint8_t *d, uint8_t *g,
+                                             int gpitch) {
+    const int W = (w + 1) >> 1, H = (h + 1) >> 1;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int Y = threadIdx.x >> 5; Y < H; Y += nw) {
+        const uint8_t *rows[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) rows[k] = s + refl101(2 * Y + k - 2, h) * stride;
+        for (int X = lane; X < W; X += 32) {
+            int cols[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) cols[k] = refl101(2 * X + k - 2, w);
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const uint8_t *r = rows[j];
+                const uint32_t v = r[cols[0]] + r[cols[4]] + 4u * (r[cols[1]] + r[cols[3]]) + 6u * r[cols[2]];
+                acc += (j == 2 ? 6u : (j == 1 || j == 3 ? 4u : 1u)) * v;
+            }
+            const uint8_t o = (uint8_t)((acc + 128u) >> 8);
+            d[Y * W + X] = o;
+            g[(size_t)Y * gpitch + X] = o;
+        }
+    }
+}
+
+// The tail of each frame's pyramid: the levels from c (the first level of at
+// most kTailMaxPx pixels) down to the last, with their Scharr planes, from
+// level c held in shared memory.  A frame's tail is split in `parts` row
+// bands of level c's gradients, one CTA each; part 0 also builds the levels
+// below c.  Level c comes from the tiled launches, or for c = 0 from the
+// caller's image (part 0 then writes the level-0 copy).  A last level too
+// large for shared memory (a large one-level pyramid) gets its Scharr planes
+// tile by tile from global memory.
+template <int GT>
+__global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
+    extern __shared__ __align__(16) uint8_t tail_smem[];
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
-    const int njobs = H->njobs[VT_MAX_LEVELS - 1], tiles = H->ntiles[VT_MAX_LEVELS - 1];
+    const int njobs = H->njobs[VT_MAX_LEVELS - 1];
     const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
     const BLvlJob *jobs =
         reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)(VT_MAX_LEVELS - 1) * H->cap_frames;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const BLvlJob jb = jobs[find_job(jobs, njobs, t)];
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const BLvlJob jb = jobs[j];
         const BFrame fr = frames[jb.frame];
-        const int l = fr.levels - 1;
-        const Level lv = fr.lv[l];
-        const int tt = t - jb.tile0;
-        const int ty = tt / jb.tiles_x, tx = tt - ty * jb.tiles_x;
-        if (l == 0)
-            scharr_tile<GT>(fr.img, lv.w, lv.h, fr.pitch, fr.vec_ok, lv.grad, lv.gpitch, lv.img, lv.pitch, tx, ty,
-                            s_in);
-        else
-            scharr_tile<GT>(lv.img, lv.w, lv.h, lv.pitch, true, lv.grad, lv.gpitch, nullptr, 0, tx, ty, s_in);
+        const int c = jb.aux;
+        const int part = jb.tiles_x, parts = jb.tile0;  // tail lists: band index and band count
+        const Level Lc = fr.lv[c];
+        const uint8_t *src = c == 0 ? fr.img : Lc.img;
+        const int sp = c == 0 ? fr.pitch : Lc.pitch;
+        if ((long)Lc.pitch * Lc.h <= kTailMaxPx) {
+            // level c in shared memory with the pyramid's row pitch
+            uint8_t *cur = tail_smem, *nxt = tail_smem + TAIL_A;
+            if (c > 0) {  // a pyramid level: 16-byte aligned rows
+                const int n16 = Lc.pitch * Lc.h / 16;
+                const uint4 *g4 = reinterpret_cast<const uint4 *>(Lc.img);
+                uint4 *s4 = reinterpret_cast<uint4 *>(cur);
+                for (int i = threadIdx.x; i < n16; i += blockDim.x) s4[i] = __ldg(g4 + i);
+            } else {  // the caller's image: any alignment
+                const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                for (int y = threadIdx.x >> 5; y < Lc.h; y += nw) {
+                    const uint8_t *sr = src + (size_t)y * sp;
+                    for (int x = lane; x < Lc.w; x += 32) {
+                        const uint8_t v = sr[x];
+                        cur[y * Lc.pitch + x] = v;
+                        if (part == 0) Lc.img[(size_t)y * Lc.pitch + x] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            const int band = (Lc.h + parts - 1) / parts;
+            const int y0 = part * band, y1 = min(Lc.h, y0 + band);
+            tail_scharr<GT>(cur, Lc.pitch, Lc.w, Lc.h, y0, y1, Lc.grad, Lc.gpitch);
+            if (part == 0) {
+                int stride = Lc.pitch;
+                for (int l = c; l + 1 < fr.levels; ++l) {
+                    const Level L = fr.lv[l], N = fr.lv[l + 1];
+                    tail_pyrdown(cur, stride, L.w, L.h, nxt, N.img, N.pitch);
+                    __syncthreads();
+                    tail_scharr<GT>(nxt, N.w, N.w, N.h, 0, N.h, N.grad, N.gpitch);
+                    uint8_t *t = cur;
+                    cur = nxt;
+                    nxt = t;
+                    stride = N.w;
+                }
+            }
+        } else if (part == 0) {
+            uint8_t (*s_in)[SC_IW] = reinterpret_cast<uint8_t (*)[SC_IW]>(tail_smem);
+            int tiles_x;
+            const int tiles = scharr_tiles(Lc.w, Lc.h, tiles_x);
+            for (int t = 0; t < tiles; ++t) {
+                const int ty = t / tiles_x, tx = t - ty * tiles_x;
+                scharr_tile<GT>(src, Lc.w, Lc.h, sp, c == 0 ? fr.vec_ok != 0 : true, Lc.grad, Lc.gpitch,
+                                c == 0 ? Lc.img : nullptr, Lc.pitch, tx, ty, s_in);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -299,30 +519,36 @@ int pyr_tiles(int w, int h, int &tiles_x) {
     return tiles_x * ((H + PD_TH - 1) / PD_TH);
 }
 
-int scharr_tiles(int w, int h, int &tiles_x) {
+__host__ __device__ int scharr_tiles(int w, int h, int &tiles_x) {
     tiles_x = (w + SC_TW - 1) / SC_TW;
     return tiles_x * ((h + SC_TH - 1) / SC_TH);
 }
 
-vt_status launch_pyr_batch(const uint8_t *dev_tab, int maxL, int gtype, int grid_pyr, int grid_sc, cudaStream_t s) {
-    for (int l = 0; l + 1 < maxL; ++l) {
+vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,
+                           cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_S16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
+        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
+        attr = true;
+    }
+    for (int l = 0; l < tiled_launches; ++l) {
         if (gtype == VT_GRAD_F16)
             k_pyr_batch<VT_GRAD_F16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
         else
             k_pyr_batch<VT_GRAD_S16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
     }
     if (gtype == VT_GRAD_F16)
-        k_scharr_batch<VT_GRAD_F16><<<grid_sc, SC_THREADS, 0, s>>>(dev_tab);
+        k_pyr_tail<VT_GRAD_F16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
     else
-        k_scharr_batch<VT_GRAD_S16><<<grid_sc, SC_THREADS, 0, s>>>(dev_tab);
+        k_pyr_tail<VT_GRAD_S16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 
 int pyr_batch_blocks_per_sm() {
-    int a = 0, b = 0;
+    int a = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pyr_batch<VT_GRAD_S16>, PD_THREADS, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scharr_batch<VT_GRAD_S16>, SC_THREADS, 0);
-    return a < b ? a : b;
+    return a;
 }
 
 void add_pyr_job(PyrJobs &jobs, int &blocks, const Level &src, const Level &dst, bool with_grad) {
