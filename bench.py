@@ -62,6 +62,23 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_seed(seed, rank):
+    """Seed of a rank's own streams: replicas track different streams."""
+    return seed + 1000 * rank
+
+
+def reduce_over_ranks(x, op, dist=None, device="cpu"):
+    """max / sum of a host scalar over all ranks (identity without a
+    process group); only timings and counts cross ranks, never data."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def pingpong(t, F):
     if F <= 1:
         return 0
@@ -141,10 +158,10 @@ class ClockSampler:
 def run_native(a, rank, world, local_rank):
     import numpy as np
 
-    specs, frames = make_workload(a.streams, a.frames, a.seed + 1000 * rank, os.cpu_count() or 1)
+    specs, frames = make_workload(a.streams, a.frames, rank_seed(a.seed, rank), os.cpu_count() or 1)
     served_wl = None
     if not a.no_served:
-        served_wl = make_workload(a.served_streams, a.frames, a.seed + 1 + 1000 * rank, os.cpu_count() or 1)
+        served_wl = make_workload(a.served_streams, a.frames, rank_seed(a.seed + 1, rank), os.cpu_count() or 1)
 
     import torch
 
@@ -228,18 +245,10 @@ def run_native(a, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return reduce_over_ranks(x, "max", dist, dev)
 
     def sum_over_ranks(x):
-        if dist is None:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        return float(tt.item())
+        return reduce_over_ranks(x, "sum", dist, dev)
 
     # ---------------- batched (headline) ----------------
     uuid = str(torch.cuda.get_device_properties(local_rank).uuid)

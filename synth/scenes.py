@@ -80,7 +80,12 @@ class HeightFieldScene:
     OVERSAMPLE = 2  # raster cells per texture pixel
     EXTENT = (-8.0, -6.0, 8.0, 6.0)  # metres
 
-    def __init__(self, seed: int, n_bumps: int = 40):
+    def __init__(self, seed: int, n_bumps: int = 40, texel_m: float | None = None):
+        """texel_m: size of one texture pixel on the wall; a camera with a
+        larger focal length should get a proportionally smaller texel so that
+        the texture keeps its detail per image pixel."""
+        if texel_m is not None:
+            self.TEXEL_M = float(texel_m)
         rng = np.random.Generator(np.random.PCG64(seed))
         x0, y0, x1, y1 = self.EXTENT
         self.z0 = rng.uniform(3.0, 4.0)
@@ -173,7 +178,7 @@ def make_stereo_sequence(seed: int = 2, n_frames: int = 4, w: int = 752, h: int 
     rng = np.random.Generator(np.random.PCG64(seed))
     if f is None:
         f = 460.0 * w / 752.0
-    scene = scene or HeightFieldScene(seed)
+    scene = scene or HeightFieldScene(seed, texel_m=HeightFieldScene.TEXEL_M * 460.0 / f)
     # smooth trajectory: per-axis sinusoids, peak speed <= max_speed and
     # peak rotation rate <= max_rot_deg per frame (split over three axes)
     per_axis_v = max_speed / fps / np.sqrt(3.0)

@@ -1,0 +1,146 @@
+"""Parity at the workload configurations, through the C ABI:
+
+* stereo + temporal sequence, 752x480, 1000 keypoints (NMS radius 4), 5 levels:
+  prev->cur and left->right, each forward-backward checked;
+* the precision workload, 1280x1024, 2000 keypoints, motion blur and exposure
+  change: full parity with int16 gradients, and the error of the FP16-gradient
+  variant against the FP64 oracle (on int16 gradients) stated and bounded;
+* full-size stream shapes through the batched launch the benchmark times, on
+  a sample of points the oracle tracks one by one.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import compare, oracle_margin
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_fb(I, J, pts, prm, grad):
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    pI = vt.vt_pyramid_build_grad(I, prm.levels, grad)
+    pJ = vt.vt_pyramid_build_grad(J, prm.levels, grad)
+    n = len(pts)
+    p0 = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).cuda()
+    out = torch.zeros((n, 2), device="cuda")
+    st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    err = torch.zeros(n, device="cuda")
+    vt.vt_klt_track_fb(pI, pJ, p0, prm, out, st, err)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy(), st.cpu().numpy(), err.cpu().numpy()
+    pI.free()
+    pJ.free()
+    return res
+
+
+def _oracle_fb(I, J, pts, prm):
+    return oracle.track_fb(oracle.build_pyramid(I, prm.levels), oracle.build_pyramid(J, prm.levels), pts, prm.win,
+                           prm.levels, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
+
+
+def test_stereo_temporal_sequence_752x480():
+    import paper_2607_01757_gb300 as vt
+
+    seq = synth.make_stereo_sequence(seed=2, n_frames=2, w=752, h=480, n_kp=1000)
+    prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
+    for I, J, pts, label in [(seq.left[0], seq.left[1], seq.kps[0], "temporal"),
+                             (seq.left[1], seq.right[1], seq.kps[1], "stereo")]:
+        assert len(pts) == 1000
+        g_pts, g_st, g_err = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
+        r = _oracle_fb(I, J, pts, prm)
+        st = compare(g_pts, g_st, r.fwd.pts, r.status, oracle_margin(r), label)
+        assert st["tracked_ref"] > 500, st
+
+
+@pytest.fixture(scope="module")
+def precision_seq():
+    return synth.make_config3_pair(seed=3)
+
+
+def test_precision_workload_1280x1024_int16(precision_seq):
+    import paper_2607_01757_gb300 as vt
+
+    seq = precision_seq
+    prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
+    I, J, pts = seq.left[0], seq.left[1], seq.kps[0]
+    assert len(pts) == 2000
+    g_pts, g_st, _ = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
+    r = _oracle_fb(I, J, pts, prm)
+    compare(g_pts, g_st, r.fwd.pts, r.status, oracle_margin(r), "1280x1024 int16")
+
+
+def test_precision_workload_fp16_gradients_error_stated(precision_seq):
+    """FP16 gradient storage changes the weights of b = sum r grad T and the
+    eigenvalue test by the half-precision rounding of raw/32 (relative
+    2^-11), so its flow differs from the FP64 oracle on int16 gradients by a
+    small amount and a few eigenvalue decisions near the threshold flip.
+    Measured and bounded here; the exact numbers are in the project notes."""
+    import paper_2607_01757_gb300 as vt
+
+    seq = precision_seq
+    prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
+    I, J, pts = seq.left[0], seq.left[1], seq.kps[0]
+    g_pts, g_st, _ = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_F16)
+    r = _oracle_fb(I, J, pts, prm)
+    both = (g_st == 1) & (r.status == 1)
+    d = np.hypot(*(g_pts[both] - r.fwd.pts[both]).T)
+    stats = dict(mean=float(d.mean()), p99=float(np.percentile(d, 99)), max=float(d.max()),
+                 status_agree=float((g_st == r.status).mean()), tracked=int(both.sum()))
+    print("fp16 gradients vs fp64 oracle:", stats)
+    assert stats["status_agree"] >= 0.99, stats
+    assert stats["mean"] < 0.005 and stats["p99"] < 0.02 and stats["max"] < 0.05, stats
+
+
+def test_full_size_streams_batched_sampled():
+    """The batched launch of the benchmark on full-size stream shapes (one
+    stream of each shape, stereo and mono), every point tracked on the GPU,
+    a sample of 48 points per task re-tracked by the oracle one by one."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.engine import BatchedTracker
+
+    specs = synth.make_stream_mix(32, seed=4)
+    pick = []
+    for shape in synth.scenes.STREAM_SHAPES:
+        cand = [sp for sp in specs if (sp.w, sp.h) == shape]
+        if cand:
+            pick.append(cand[0])
+    frames = [synth.render_stream_frames(sp, 2) for sp in pick]
+    prm = vt.KltParams()
+    tr = BatchedTracker(pick, prm)
+    sids = list(range(len(pick)))
+    L0 = [torch.from_numpy(f.left[0]).cuda() for f in frames]
+    L1 = [torch.from_numpy(f.left[1]).cuda() for f in frames]
+    R0 = [torch.from_numpy(f.right[0]).cuda() if f.right[0] is not None else None for f in frames]
+    R1 = [torch.from_numpy(f.right[1]).cuda() if f.right[1] is not None else None for f in frames]
+    k0 = [torch.from_numpy(f.kps[0]).cuda() for f in frames]
+    k1 = [torch.from_numpy(f.kps[1]).cuda() for f in frames]
+    n0 = [len(f.kps[0]) for f in frames]
+    n1 = [len(f.kps[1]) for f in frames]
+    tr.stage(tr.step_tables(sids, [0] * len(sids), [0] * len(sids), L0, R0))
+    tr.run(graph=False)
+    tr.advance(sids)
+    tr.stage(tr.step_tables(sids, n0, n1, L1, R1, kpt=k0, kps=k1))
+    tr.run(graph=True)
+    tr.advance(sids)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(17))
+    for i, (sp, f) in enumerate(zip(pick, frames)):
+        s = tr.streams[i]
+        prm_s = vt.KltParams(levels=sp.levels)
+        tasks = [(f.left[0], f.left[1], f.kps[0], s.out_t)]
+        if sp.stereo:
+            tasks.append((f.left[1], f.right[1], f.kps[1], s.out_s))
+        for I, J, kp, out in tasks:
+            idx = np.sort(rng.choice(len(kp), size=min(48, len(kp)), replace=False))
+            r = _oracle_fb(I, J, kp[idx], prm_s)
+            compare(out[0].cpu().numpy()[idx], out[1].cpu().numpy()[idx], r.fwd.pts, r.status, oracle_margin(r),
+                    f"{sp.w}x{sp.h} L{sp.levels}")
+    tr.free()
