@@ -216,6 +216,50 @@ VT_API vt_status vt_klt_track_fb(const vt_pyramid *prev, const vt_pyramid *cur, 
                           const vt_klt_diag *diag, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Shi-Tomasi (GFTT) corner detection on a pyramid level: the classical
+ * detector the paper pairs with LK tracking (Sec. IV; CPU-based in the paper,
+ * Sec. V-F).  It reuses the level's int16 Scharr gradients (VT_GRAD_S16).
+ *   score(x)  lambda_min of [a b; b c], a, b, c the (2 block_radius + 1)^2 box
+ *             sums of gx^2, gx gy, gy^2 (raw Scharr, reflect-101 borders),
+ *             evaluated in single precision as
+ *             ((a + c) - sqrt((a - c)^2 + 4 b^2)) / 2, clamped at 0;
+ *   candidate score >= quality * (maximum score of the level) and > 0, at
+ *             least `border` px from every edge, the maximum of its
+ *             (2 nms_radius + 1)^2 neighbourhood (a tie goes to the smaller
+ *             row-major index), squared distance >= min_dist^2 to every mask
+ *             point (e.g. points already tracked);
+ *   selection in order of score (descending, then index ascending), keep a
+ *             candidate when no kept corner is closer than min_dist; at most
+ *             max_corners.
+ * Corners (float2, integer coordinates of the level) and scores come out in
+ * that order; *count_out (a device int) receives how many.
+ * ---------------------------------------------------------------------- */
+typedef struct vt_gftt_params {
+    int max_corners;  /* 0 .. 8192 */
+    float quality;    /* relative threshold, e.g. 0.01 */
+    int min_dist;     /* >= 1 px */
+    int nms_radius;   /* >= 0 */
+    int block_radius; /* 0 .. 3 (1 = 3x3 block) */
+    int border;       /* >= 0 px */
+} vt_gftt_params;
+
+typedef struct vt_gftt vt_gftt; /* opaque: workspace for levels up to max_w x max_h */
+
+/* Allocates the workspace (score map, candidate keys). */
+VT_API vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out);
+
+/* Detect corners on level `level` of `p`.  mask_pts: device float2[n_mask]
+ * (nullable when n_mask == 0).  corners_out: device float2[max_corners];
+ * scores_out: device float[max_corners] (nullable); count_out: device int.
+ * Calls on one vt_gftt must be serialised (they share its workspace). */
+VT_API vt_status vt_gftt_detect(vt_gftt *g, const vt_pyramid *p, int level, const vt_gftt_params *prm,
+                                const float *mask_pts, int n_mask, float *corners_out, float *scores_out,
+                                int *count_out, void *cuda_stream);
+
+/* Frees the workspace (synchronises the device first; NULL is ignored). */
+VT_API void vt_gftt_free(vt_gftt *g);
+
+/* ------------------------------------------------------------------------
  * Batched tracking: the frames and tracking tasks of many independent camera
  * streams in one fixed sequence of persistent launches (one per pyramid
  * level, one for the last levels' gradients, one for every tracking task),

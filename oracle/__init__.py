@@ -36,6 +36,12 @@ def _load():
         lib.orc_track.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, f64p, C.c_void_p, C.c_int,
                                   f64p, u8p, f64p, u8p, i32p, f64p, f64p]
         lib.orc_fb_check.argtypes = [f64p, f64p, u8p, u8p, C.c_int, C.c_double, u8p, f64p, f64p]
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+        lib.orc_gftt.restype = C.c_int
+        lib.orc_gftt.argtypes = [i16p, i16p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_int, C.c_int,
+                                 C.c_int, C.c_void_p, C.c_int, C.c_int, i32p, f32p]
+        lib.orc_gftt_score.restype = C.c_float
+        lib.orc_gftt_score.argtypes = [C.c_long, C.c_long, C.c_long]
         _lib = lib
     return _lib
 
@@ -197,3 +203,23 @@ def track_fb(pI: Pyramid, pJ: Pyramid, pts, win=21, levels=None, max_iters=30, e
     reason[(reason == 0)] = b.reason[(reason == 0)]
     reason[(reason == 0) & (st == 0)] = LOST_FB
     return FBResult(f, b, st, reason, d, m)
+
+
+def gftt(gx, gy, max_corners=150, quality=0.01, min_dist=10, nms_radius=4, block_radius=1, border=10, mask=None):
+    """Shi-Tomasi corners of one level from its raw int16 Scharr planes (the
+    reading is stated in orc.c).  Returns (corners int32 [k, 2], scores
+    float32 [k]) in priority order."""
+    gx = np.ascontiguousarray(gx, np.int16)
+    gy = np.ascontiguousarray(gy, np.int16)
+    h, w = gx.shape
+    m = None if mask is None else np.ascontiguousarray(mask, np.float64).reshape(-1, 2)
+    out = np.zeros((max(1, max_corners), 2), np.int32)
+    sc = np.zeros(max(1, max_corners), np.float32)
+    k = _load().orc_gftt(gx, gy, w, h, w, block_radius, quality, nms_radius, border, min_dist,
+                         None if m is None else m.ctypes.data, 0 if m is None else len(m), max_corners, out, sc)
+    return out[:k].copy(), sc[:k].copy()
+
+
+def gftt_score(a, b, c):
+    """Single-precision minimum eigenvalue of [[a, b], [b, c]] as the detector evaluates it."""
+    return float(_load().orc_gftt_score(int(a), int(b), int(c)))

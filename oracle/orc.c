@@ -280,3 +280,131 @@ void orc_fb_check(const double *p0, const double *p0b, const uint8_t *st_f, cons
         status[i] = (uint8_t)(st_f[i] && st_b[i] && d <= thr);
     }
 }
+
+/*
+ * Shi-Tomasi (GFTT) corner detection: the paper's classical front-end pairs
+ * Shi-Tomasi corners with LK tracking (Sec. IV) and runs it on the CPU
+ * (Sec. V-F).  Reading implemented (the paper gives no parameters):
+ *   gradients   raw Scharr int16 of the level (gx, gy);
+ *   tensor      a = sum gx^2, b = sum gx gy, c = sum gy^2 over the
+ *               (2 br + 1)^2 block around the pixel, reflect-101 borders,
+ *               exact integers;
+ *   score       lambda = ((a + c) - sqrt((a - c)^2 + 4 b^2)) / 2 evaluated in
+ *               single precision, operation by operation (so that every
+ *               decision below is the same as the CUDA kernel's), clamped
+ *               at 0;
+ *   candidate   lambda >= quality * max(lambda) and lambda > 0, at least
+ *               `border` px from every image edge, a local maximum of its
+ *               (2 nms + 1)^2 neighbourhood (ties: the smaller row-major
+ *               index wins), and at squared distance >= min_dist^2 from
+ *               every mask point (points already tracked);
+ *   selection   candidates in priority order (lambda descending, index
+ *               ascending); a candidate is kept when no kept corner lies at
+ *               squared distance < min_dist^2; at most max_corners are kept.
+ * Output: kept corners in priority order (x, y integers) and their scores.
+ */
+float orc_gftt_score(long a, long b, long c)
+{
+    const float fa = (float)a, fb = (float)b, fc = (float)c;
+    const volatile float d = fa - fc;
+    const volatile float d2 = d * d;
+    const volatile float b2 = fb * fb;
+    const volatile float b4 = 4.0f * b2;
+    const volatile float q = d2 + b4;
+    const volatile float r = sqrtf(q);
+    const volatile float s = fa + fc;
+    const volatile float t = s - r;
+    const float l = 0.5f * t;
+    return l > 0.0f ? l : 0.0f;
+}
+
+int orc_gftt(const int16_t *gx, const int16_t *gy, int w, int h, int gpitch, int br, float quality, int nms,
+             int border, int min_dist, const double *mask, int n_mask, int max_corners, int32_t *out_xy,
+             float *out_score)
+{
+    float *score = (float *)malloc(sizeof(float) * (size_t)w * h);
+    float mx = 0.0f;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            long a = 0, b = 0, c = 0;
+            for (int j = -br; j <= br; ++j)
+                for (int i = -br; i <= br; ++i) {
+                    const long o = (long)refl101(y + j, h) * gpitch + refl101(x + i, w);
+                    const long u = gx[o], v = gy[o];
+                    a += u * u;
+                    b += u * v;
+                    c += v * v;
+                }
+            const float s = orc_gftt_score(a, b, c);
+            score[(long)y * w + x] = s;
+            if (s > mx) mx = s;
+        }
+    const volatile float thr = quality * mx;
+    /* candidates */
+    long cap = 1024, n = 0;
+    long *cand = (long *)malloc(sizeof(long) * cap);
+    for (int y = border; y < h - border; ++y)
+        for (int x = border; x < w - border; ++x) {
+            const long idx = (long)y * w + x;
+            const float s = score[idx];
+            if (!(s >= thr) || !(s > 0.0f)) continue;
+            int ok = 1;
+            for (int j = -nms; j <= nms && ok; ++j)
+                for (int i = -nms; i <= nms; ++i) {
+                    const int yy = y + j, xx = x + i;
+                    if ((i == 0 && j == 0) || yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                    const long q = (long)yy * w + xx;
+                    const float t = score[q];
+                    if (t > s || (t == s && q < idx)) {
+                        ok = 0;
+                        break;
+                    }
+                }
+            for (int m = 0; m < n_mask && ok; ++m) {
+                const volatile float dx = (float)x - (float)mask[2 * m];
+                const volatile float dy = (float)y - (float)mask[2 * m + 1];
+                const volatile float dd = dx * dx + dy * dy;
+                if (dd < (float)(min_dist * min_dist)) ok = 0;
+            }
+            if (!ok) continue;
+            if (n == cap) {
+                cap *= 2;
+                cand = (long *)realloc(cand, sizeof(long) * cap);
+            }
+            cand[n++] = idx;
+        }
+    /* priority order: score descending, index ascending (insertion into a
+     * sorted array is plain and obviously right; n is small) */
+    for (long i = 1; i < n; ++i) {
+        const long v = cand[i];
+        long j = i - 1;
+        while (j >= 0) {
+            const long u = cand[j];
+            const int before = score[v] > score[u] || (score[v] == score[u] && v < u);
+            if (!before) break;
+            cand[j + 1] = u;
+            --j;
+        }
+        cand[j + 1] = v;
+    }
+    int kept = 0;
+    for (long i = 0; i < n && kept < max_corners; ++i) {
+        const int x = (int)(cand[i] % w), y = (int)(cand[i] / w);
+        int ok = 1;
+        for (int k = 0; k < kept; ++k) {
+            const long dx = x - out_xy[2 * k], dy = y - out_xy[2 * k + 1];
+            if (dx * dx + dy * dy < (long)min_dist * min_dist) {
+                ok = 0;
+                break;
+            }
+        }
+        if (!ok) continue;
+        out_xy[2 * kept] = x;
+        out_xy[2 * kept + 1] = y;
+        out_score[kept] = score[cand[i]];
+        ++kept;
+    }
+    free(cand);
+    free(score);
+    return kept;
+}

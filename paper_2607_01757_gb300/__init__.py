@@ -6,4 +6,4 @@ the library and fails loudly if it is missing.
 """
 
 from .vt import *  # noqa: F401,F403
-from .vt import Pyramid, Batch, KltParams, VTError, LIB_PATH, header_functions  # noqa: F401
+from .vt import Pyramid, Batch, Gftt, GfttParams, KltParams, VTError, LIB_PATH, header_functions  # noqa: F401

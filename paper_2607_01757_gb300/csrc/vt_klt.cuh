@@ -256,8 +256,8 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
 // Track one point u = (ux0, uy0) from pyramid I to pyramid J.
 template <int WIN, int GT>
 __device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
-                                            bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm,
-                                            KOut &o) {
+                                            bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm, KOut &o,
+                                            bool want_err = true) {
     constexpr int HW = WIN / 2;
     constexpr float N = (float)(WIN * WIN);
     constexpr float unit = grad_unit<GT>();
@@ -378,8 +378,10 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             o.reason = VT_LOST_OOB;
         } else {
             // T still holds level 0's template
-            o.err = abs_residual<WIN>(J[0], o.x, o.y, lane, T, sm) / N;
-            ++o.errp;
+            if (want_err) {
+                o.err = abs_residual<WIN>(J[0], o.x, o.y, lane, T, sm) / N;
+                ++o.errp;
+            }
         }
     }
 }
@@ -398,7 +400,8 @@ __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, 
 #pragma unroll 1
     for (int pass = 0; pass < npass; ++pass) {
         KOut r;
-        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r);
+        // the backward pass only decides the status: its error is not an output
+        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r, pass == 0);
         if (pass == 0) {
             o = r;
             if (!r.status) return;

@@ -412,3 +412,68 @@ def vt_klt_track_tasks_noalloc(tasks, params: KltParams, stream=None) -> None:
     prm = params.c()
     _check(_lib.vt_klt_track_tasks_noalloc(ta, len(tasks), C.byref(prm), _stream(stream)),
            "vt_klt_track_tasks_noalloc")
+
+
+# ------------------------------------------------------------------ GFTT
+class vt_gftt_params(C.Structure):
+    _fields_ = [("max_corners", i32), ("quality", f32), ("min_dist", i32), ("nms_radius", i32),
+                ("block_radius", i32), ("border", i32)]
+
+
+_sig("vt_gftt_create", i32, [i32, i32, C.POINTER(vp)])
+_sig("vt_gftt_free", None, [vp])
+_sig("vt_gftt_detect", i32, [vp, vp, i32, C.POINTER(vt_gftt_params), vp, i32, vp, vp, vp, vp])
+
+
+@dataclass
+class GfttParams:
+    max_corners: int = 150
+    quality: float = 0.01
+    min_dist: int = 10
+    nms_radius: int = 4
+    block_radius: int = 1
+    border: int = 10
+
+    def c(self) -> vt_gftt_params:
+        return vt_gftt_params(self.max_corners, self.quality, self.min_dist, self.nms_radius, self.block_radius,
+                              self.border)
+
+
+class Gftt:
+    """Owning handle of a vt_gftt detector workspace."""
+
+    def __init__(self, max_w: int, max_h: int):
+        hd = vp()
+        _check(_lib.vt_gftt_create(max_w, max_h, C.byref(hd)), "vt_gftt_create")
+        self.handle = hd.value
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+    def free(self):
+        if self.handle:
+            _lib.vt_gftt_free(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def vt_gftt_create(max_w: int, max_h: int) -> Gftt:
+    return Gftt(max_w, max_h)
+
+
+def vt_gftt_free(g: Gftt) -> None:
+    g.free()
+
+
+def vt_gftt_detect(g: Gftt, pyr: Pyramid, level: int, params: GfttParams, corners_out, count_out, scores_out=None,
+                   mask=None, stream=None) -> None:
+    prm = params.c()
+    n_mask = 0 if mask is None else int(mask.shape[0])
+    _check(_lib.vt_gftt_detect(g, pyr, level, C.byref(prm), _ptr(mask), n_mask, _ptr(corners_out),
+                               _ptr(scores_out), _ptr(count_out), _stream(stream)), "vt_gftt_detect")
