@@ -34,6 +34,11 @@ METRIC = "tracked features/s & p99 frame latency, batched/served vs plain KLT, 1
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
+# DRAM bytes (read + write) per launch from one ncu capture of the default
+# workload (32 streams, 4 frames, seed 4; dram__bytes_read.sum +
+# dram__bytes_write.sum, caches flushed before each captured launch), summarised
+# in profiles/launches_bench_32streams.md.  Reported only for that workload.
+NCU_TRAFFIC_BYTES = {"k_klt_batch": 431.18e6 + 0.87e6, "pyramid": 83.2e6 + 271.4e6}
 SM_MAX_MHZ = 2070.0
 
 
@@ -52,6 +57,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="4 streams, for profiler captures")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-gftt", action="store_true")
+    ap.add_argument("--no-gate", action="store_true")
     ap.add_argument("--served-streams", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=10000)
     ap.add_argument("--served-budget-gb", type=float, default=20.0)
@@ -166,6 +173,7 @@ def run_native(a, rank, world, local_rank):
     import torch
 
     import paper_2607_01757_gb300 as vt
+    import synth
     from paper_2607_01757_gb300.engine import BatchedTracker
 
     torch.cuda.set_device(local_rank)
@@ -178,7 +186,9 @@ def run_native(a, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     F = a.frames
     prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
-    tr = BatchedTracker(specs, prm)
+    gprm = vt.GateParams(min_disp=1.0, z_min=0.1, z_max=50.0, max_reproj=1.5)
+    rigs = [vt.StereoRig(*synth.stream_rig(sp)) if sp.stereo else None for sp in specs]
+    tr = BatchedTracker(specs, prm, gate=gprm, rigs=rigs)
     S = len(specs)
     sids = list(range(S))
     # device frame store: frames and keypoints of every stream
@@ -202,22 +212,22 @@ def run_native(a, rank, world, local_rank):
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def batched_prepare(t, flops=None):
+    def batched_prepare(t, flops=None, gate=False):
         # host-only: job tables of step t into the pinned staging buffer
         L, R, kt, ks, n_t, n_s = step_args(t)
-        tr.stage(tr.step_tables(sids, n_t, n_s, L, R, flops=flops, kpt=kt, kps=ks))
+        tr.stage(tr.step_tables(sids, n_t, n_s, L, R, flops=flops, kpt=kt, kps=ks, gate=gate))
 
     def batched_launch(t, events=None, graph=True):
         tr.run(stream, graph=graph, events=events)
         tr.advance(sids)
 
-    def batched_step(t, events=None, graph=True, flops=None):
-        batched_prepare(t, flops)
+    def batched_step(t, events=None, graph=True, flops=None, gate=False):
+        batched_prepare(t, flops, gate)
         batched_launch(t, events, graph)
 
     def plain_step(t):
         L, R, kt, ks, n_t, n_s = step_args(t)
-        tr.plain_step(sids, n_t, n_s, L, R, stream, kpt=kt, kps=ks)
+        tr.plain_step(sids, n_t, n_s, L, R, stream, kpt=kt, kps=ks, gate=False)
         tr.advance(sids)
 
     def timed(fn, t0, K, prepare=None, flush_between=True):
@@ -340,8 +350,41 @@ def run_native(a, rank, world, local_rank):
             peaks = json.load(f)
     except OSError:
         pass
+    default_wl = (a.streams, a.frames, a.seed) == (32, 4, 4) and world == 1
+    traffic = NCU_TRAFFIC_BYTES if default_wl else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # ---------------- stereo triangulation gate (a further row, outside the headline step) -----
+    gate = None
+    if not a.no_gate:
+        for _ in range(2):
+            batched_step(t, gate=True)
+            t += 1
+        gms, gsteps, gate_ms, pairs, kept, tracked = [], [], [], 0, 0, 0
+        for i in range(a.steps):
+            flush.fill_(i & 0xFF)
+            e = [ev(), ev(), ev(), ev()]
+            batched_step(t, events=e, gate=True)
+            e_end = ev()
+            torch.cuda.synchronize()
+            gsteps.append(e[0].elapsed_time(e_end))
+            gate_ms.append(e[3].elapsed_time(e_end))
+            _, _, _, _, n_t_, n_s_ = step_args(t)
+            for k, s in enumerate(tr.streams):
+                if s.rig is not None and n_s_[k] > 0:
+                    pairs += n_s_[k]
+                    kept += int(s.gate_out[0][:n_s_[k]].sum().item())
+                    tracked += int(s.out_s[1][:n_s_[k]].sum().item())
+            t += 1
+        gate = {"kernel": "k_gate_batch", "launch_ms": statistics.mean(gate_ms),
+                "pairs_per_step": pairs // a.steps, "pairs_per_s": pairs / (sum(gate_ms) / 1e3),
+                "gated_step_ms": statistics.mean(gsteps),
+                "kept_of_flow_checked": kept / max(1, tracked),
+                "params": {"min_disp_px": gprm.min_disp, "z_min_m": gprm.z_min, "z_max_m": gprm.z_max,
+                           "max_reproj_px": gprm.max_reproj},
+                "timing": "CUDA events from the end of the tracking launch to the end of the run, "
+                          "direct launches, L2 flushed between steps"}
 
     # ---------------- plain path ----------------
     plain = None
@@ -357,7 +400,7 @@ def run_native(a, rank, world, local_rank):
         L_, R_, kt_, ks_, n_t_, n_s_ = step_args(t)
         plain = {"value": sum_over_ranks(pfeats) / (ptot / 1e3), "ms_per_step": ptot / a.steps,
                  "p50_ms": float(np.percentile(pms, 50)), "p99_ms": float(np.percentile(pms, 99)),
-                 "gpu_launches_per_step": tr.plain_launches(sids, n_t_, n_s_)}
+                 "gpu_launches_per_step": tr.plain_launches(sids, n_t_, n_s_, gate=False)}
 
     # ---------------- end to end: host frames in, host results out ----------------
     e2e = None
@@ -386,7 +429,7 @@ def run_native(a, rank, world, local_rank):
                     s.in_right.copy_(hright[i][fc], non_blocking=True)
                     s.kp_s[:n_s[i]].copy_(hkps[i][fc], non_blocking=True)
                     h2d["b"] += s.w * s.h + 8 * n_s[i]
-            tr.stage(tr.step_tables(sids, n_t, n_s))
+            tr.stage(tr.step_tables(sids, n_t, n_s, gate=False))
             tr.run(stream, graph=True)
             tr.advance(sids)
             for i, s in enumerate(tr.streams):
@@ -424,6 +467,11 @@ def run_native(a, rank, world, local_rank):
     served = None
     if served_wl is not None:
         served = run_served(a, served_wl, prm, barrier, max_over_ranks, sum_over_ranks)
+
+    # ---------------- GFTT detection (next row: detector feeding the tracker) ---
+    gftt = None
+    if not a.no_gftt and rank == 0:
+        gftt = run_gftt(specs, frames)
 
     # ---------------- CPU baseline (oracle), rank 0 at N = 1 only -------------
     cpu = None
@@ -465,14 +513,19 @@ def run_native(a, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": a.steps * launches_per_step,
         "roofline": {"bound": "alu", "kernel": "k_klt_batch", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic.get("k_klt_batch"),
                      "flops_per_launch": klt_flops, "launch_ms": klt_avg_s * 1e3,
+                     "traffic_note": "DRAM bytes per launch, one ncu capture (cold caches), default workload only",
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "roofline_pyramid": {"bound": "hbm", "kernel": "k_pyr_batch+k_pyr_tail", "achieved": pyr_bytes / pyr_avg_s
                              / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": None,
-                             "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src},
+                             "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": traffic.get("pyramid"),
+                             "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src,
+                             "traffic_note": "DRAM bytes of the step's pyramid launches, one ncu capture (cold "
+                                             "caches), default workload only"},
         "served": served,
+        "gftt": gftt,
+        "stereo_gate": gate,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -534,6 +587,48 @@ def run_served(a, wl, prm, barrier, max_over_ranks, sum_over_ranks):
     sb["budget_bytes"] = tight
     out["batched_quarter_budget"] = sb
     srv.free()
+    return out
+
+
+def run_gftt(specs, frames):
+    """Shi-Tomasi detection on level 0 of one frame of each stream shape
+    (CUDA events, median of 10 after 3 warm-ups), with the oracle's time on
+    the same frame for reference."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2607_01757_gb300 as vt
+
+    out = []
+    seen = set()
+    for sp, fr in zip(specs, frames):
+        if (sp.w, sp.h) in seen:
+            continue
+        seen.add((sp.w, sp.h))
+        prm = vt.GfttParams(max_corners=sp.n_kp, quality=0.01, min_dist=8, nms_radius=4, block_radius=1, border=10)
+        p = vt.vt_pyramid_build_grad(fr.left[0], 1, vt.VT_GRAD_S16)
+        g = vt.Gftt(sp.w, sp.h)
+        xy = torch.zeros((sp.n_kp, 2), device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ms = []
+        for i in range(13):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            vt.vt_gftt_detect(g, p, 0, prm, xy, cnt)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 3:
+                ms.append(e0.elapsed_time(e1))
+        rp = oracle.build_pyramid(fr.left[0], 1)
+        t0 = time.perf_counter()
+        oracle.gftt(rp.gx[0], rp.gy[0], prm.max_corners, prm.quality, prm.min_dist, prm.nms_radius,
+                    prm.block_radius, prm.border)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        out.append({"shape": f"{sp.w}x{sp.h}", "max_corners": sp.n_kp, "corners": int(cnt.item()),
+                    "gpu_ms": float(np.median(ms)), "oracle_ms": cpu_ms})
+        g.free()
+        p.free()
     return out
 
 

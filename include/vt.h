@@ -67,7 +67,11 @@ enum {
     VT_LOST_EIG = 1,   /* lambda_min(G) below threshold, or det(G) <= 0 */
     VT_LOST_OOB = 2,   /* estimate left the image (see vt_klt_track) */
     VT_LOST_FB = 3,    /* forward-backward distance above threshold */
-    VT_LOST_INPUT = 4  /* input point outside [0, W-1] x [0, H-1] or NaN */
+    VT_LOST_INPUT = 4, /* input point outside [0, W-1] x [0, H-1] or NaN; for
+                          vt_stereo_gate: pair not tracked or not finite */
+    VT_LOST_DISP = 5,  /* stereo gate: negligible disparity */
+    VT_LOST_DEPTH = 6, /* stereo gate: depth outside the valid range (or behind a camera) */
+    VT_LOST_REPROJ = 7 /* stereo gate: reprojection error above the bound in a view */
 };
 
 enum { VT_MAX_LEVELS = 8 };      /* levels per pyramid */
@@ -260,6 +264,53 @@ VT_API vt_status vt_gftt_detect(vt_gftt *g, const vt_pyramid *p, int level, cons
 VT_API void vt_gftt_free(vt_gftt *g);
 
 /* ------------------------------------------------------------------------
+ * Stereo triangulation gate: the geometric check of stereo correspondences
+ * (Sec. III-C: matches with negligible disparity are dropped; the others are
+ * triangulated with the rig's extrinsics and kept only when the point has a
+ * positive depth inside a valid range and reprojects to within 1.5 px of the
+ * observation in both views).  Applied here to the left->right LK
+ * correspondences, one per point, after the cross-camera flow check.
+ * Reading (the paper fixes only the 1.5 px), evaluated in FP64:
+ *   disparity |p_R - pi_R(R K_L^-1 (p_L, 1))|: distance in the right image
+ *             from the image of the left ray's point at infinity (infinite
+ *             when that point is behind the right camera); kept when
+ *             > min_disp, else VT_LOST_DISP;
+ *   point     linear (DLT) two-view triangulation on normalised coordinates
+ *             with P_L = [I | 0], P_R = [R | t]: the unit X minimising
+ *             |A X|, A's rows x P^3 - P^1 and y P^3 - P^2 of each view;
+ *   depth     X_4 != 0, Z_R > 0 and z_min <= Z_L <= z_max, else
+ *             VT_LOST_DEPTH;
+ *   reprojection  |pi_L(X) - p_L| <= max_reproj and |pi_R(R X + t) - p_R| <=
+ *             max_reproj (pixels, each view), else VT_LOST_REPROJ.
+ * An untracked (status_in == 0) or non-finite pair is VT_LOST_INPUT.
+ * ---------------------------------------------------------------------- */
+typedef struct vt_stereo_rig {
+    double kl[4]; /* left pinhole fx, fy, cx, cy (px); observations undistorted */
+    double kr[4]; /* right pinhole fx, fy, cx, cy (px) */
+    double R[9];  /* row-major rotation, left-camera to right-camera coordinates */
+    double t[3];  /* translation in metres: X_R = R X_L + t */
+} vt_stereo_rig;
+
+typedef struct vt_gate_params {
+    double min_disp;   /* px, >= 0: kept when disparity > min_disp */
+    double z_min;      /* m: kept when z_min <= Z_L ... */
+    double z_max;      /* ... <= z_max (z_min <= z_max; z_max may be +inf) */
+    double max_reproj; /* px, >= 0: 1.5 in the paper */
+} vt_gate_params;
+
+/* pts_l, pts_r: device float2[n] (left observation, right observation);
+ * status_in: device uint8[n], nullable (all tracked); xyz_out: device
+ * float[3 n], nullable: the triangulated point in the left-camera frame when
+ * triangulation ran (0 for VT_LOST_INPUT / VT_LOST_DISP or X_4 == 0);
+ * status_out: device uint8[n], 1 kept / 0 rejected (may alias status_in);
+ * reason_out: device uint8[n], nullable.  rig and prm are host pointers read
+ * during the call.  VT_ERR_ARG for n < 0, a missing array, non-finite rig
+ * values, a zero focal length or out-of-range parameters. */
+VT_API vt_status vt_stereo_gate(const float *pts_l, const float *pts_r, const uint8_t *status_in, int n,
+                                const vt_stereo_rig *rig, const vt_gate_params *prm, float *xyz_out,
+                                uint8_t *status_out, uint8_t *reason_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Batched tracking: the frames and tracking tasks of many independent camera
  * streams in one fixed sequence of persistent launches (one per pyramid
  * level, one for the last levels' gradients, one for every tracking task),
@@ -321,6 +372,30 @@ VT_API vt_status vt_batch_config(vt_batch *b, int klt_warps_per_cta, int klt_cta
  */
 VT_API vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_grad_type gtype,
                               const vt_track_task *tasks, int ntasks, const vt_klt_params *prm);
+
+/* One stereo-gate task of a batched run (vt_stereo_gate semantics): pairs
+ * (pts_l[i], pts_r[i]) of one rig.  The arrays may be outputs of the same
+ * run's tracking tasks (e.g. pts_r = a left->right task's pts_out and
+ * status_in its status): the gate runs after the tracking launch. */
+typedef struct vt_gate_task {
+    const float *pts_l;       /* device float2[n] */
+    const float *pts_r;       /* device float2[n] */
+    const uint8_t *status_in; /* device uint8[n], nullable */
+    int n;
+    vt_stereo_rig rig;   /* copied into the staged tables */
+    float *xyz;          /* device float[3 n], nullable */
+    uint8_t *status_out; /* device uint8[n] (may alias status_in) */
+    uint8_t *reason;     /* device uint8[n], nullable */
+} vt_gate_task;
+
+/*
+ * Add stereo-gate tasks to the run staged by the last vt_batch_set (before it
+ * is run; VT_ERR_ARG otherwise).  They run as one more launch after the
+ * tracking launch, one thread per pair, with parameters `prm` (host pointer,
+ * copied).  At most max_tasks gate tasks.  A vt_batch_set without this call
+ * stages a run without gates.
+ */
+VT_API vt_status vt_batch_set_gates(vt_batch *b, const vt_gate_task *gates, int ngates, const vt_gate_params *prm);
 
 /* Run the staged batch with direct launches on `cuda_stream`.  Runs of one
  * batch must be issued on one stream (or otherwise serialised). */

@@ -6,4 +6,5 @@ the library and fails loudly if it is missing.
 """
 
 from .vt import *  # noqa: F401,F403
-from .vt import Pyramid, Batch, Gftt, GfttParams, KltParams, VTError, LIB_PATH, header_functions  # noqa: F401
+from .vt import (Pyramid, Batch, Gftt, GfttParams, GateParams, KltParams, StereoRig, VTError, LIB_PATH,  # noqa: F401
+                 header_functions)

@@ -7,6 +7,8 @@
 //   K2    Scharr of each frame's last level
 //   K3    one persistent KLT launch: warps take points from a device work
 //         counter (one atomicAdd per point) across all tasks
+//   K7    (when gate tasks are set) the stereo triangulation gate over every
+//         gate task's pairs, one thread per pair
 //
 // Grid sizes do not depend on the batch (SMs x resident CTAs), so one CUDA
 // graph per topology (deepest pyramid, gradient type, window) replays any
@@ -94,10 +96,10 @@ static KltBatchKernel klt_batch_kernel(int win, int gtype, int warps) {
 }
 
 struct Topo {
-    int maxL, gtype, win, klt_warps, klt_grid, pyr_grid;
+    int maxL, gtype, win, klt_warps, klt_grid, pyr_grid, gate;
     bool operator==(const Topo &o) const {
         return maxL == o.maxL && gtype == o.gtype && win == o.win && klt_warps == o.klt_warps &&
-               klt_grid == o.klt_grid && pyr_grid == o.pyr_grid;
+               klt_grid == o.klt_grid && pyr_grid == o.pyr_grid && gate == o.gate;
     }
 };
 
@@ -115,6 +117,7 @@ struct vt_batch {
     bool ev_used[2];
     int next;    // buffer the next vt_batch_set writes
     int staged;  // buffer with the latest staged tables, -1 if none
+    bool fresh;  // the staged tables have not been enqueued yet (gates may still be set)
     Topo topo[2];
     cudaGraphExec_t exec[2];
     Topo exec_topo[2];
@@ -124,13 +127,15 @@ struct vt_batch {
     int klt_ctas_per_sm;  // 0 = occupancy limit
     int pyr_grid;
     int tail_grid;  // CTAs of the tail launch (one frame each at a time)
+    int gate_grid;  // CTAs of the stereo-gate launch
 };
 
 namespace vt {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks, int &off_prefix, size_t &bytes) {
+static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks, int &off_prefix, int &off_gates,
+                   int &off_gprefix, size_t &bytes) {
     size_t o = align_up(sizeof(BatchHdr), 64);
     off_frames = (int)o;
     o = align_up(o + sizeof(BFrame) * F, 64);
@@ -140,6 +145,10 @@ static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks,
     off_tasks = (int)o;
     o = align_up(o + sizeof(BTask) * T, 64);
     off_prefix = (int)o;
+    o = align_up(o + sizeof(int) * T, 64);
+    off_gates = (int)o;
+    o = align_up(o + sizeof(GTask) * T, 64);
+    off_gprefix = (int)o;
     o = align_up(o + sizeof(int) * T, 256);
     bytes = o;
 }
@@ -169,7 +178,9 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
     kb.fn<<<tp.klt_grid, tp.klt_warps * 32, kb.smem, s>>>(b->dev[k], b->counter + k);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
-    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return VT_ERR_CUDA;
+    if (tp.gate) return launch_gate_batch(b->dev[k], b->gate_grid, s);
+    return VT_OK;
 }
 
 }  // namespace vt
@@ -182,8 +193,8 @@ vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out) {
     if (!b) return VT_ERR_OOM;
     b->cap_frames = max_frames > 0 ? max_frames : 1;
     b->cap_tasks = max_tasks > 0 ? max_tasks : 1;
-    int of, oj, ot, op;
-    layout(b->cap_frames, b->cap_tasks, of, oj, ot, op, b->tab_bytes);
+    int of, oj, ot, op, og, ogp;
+    layout(b->cap_frames, b->cap_tasks, of, oj, ot, op, og, ogp, b->tab_bytes);
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
         ok = ok && cudaMallocHost((void **)&b->host[k], b->tab_bytes) == cudaSuccess;
@@ -204,6 +215,7 @@ vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out) {
     b->klt_ctas_per_sm = 0;
     b->tail_grid = 8 * b->cap_frames < 2 * b->sms ? 8 * b->cap_frames : 2 * b->sms;
     b->pyr_grid = b->sms * (pyr_batch_blocks_per_sm() > 0 ? pyr_batch_blocks_per_sm() : 1);
+    b->gate_grid = 4 * b->sms;
     b->staged = -1;
     *out = b;
     return VT_OK;
@@ -273,7 +285,8 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     BatchHdr *H = reinterpret_cast<BatchHdr *>(tab);
     memset(H, 0, sizeof(BatchHdr));
     size_t bytes;
-    layout(b->cap_frames, b->cap_tasks, H->off_frames, H->off_jobs, H->off_tasks, H->off_prefix, bytes);
+    layout(b->cap_frames, b->cap_tasks, H->off_frames, H->off_jobs, H->off_tasks, H->off_prefix, H->off_gates,
+           H->off_gprefix, bytes);
     H->cap_frames = b->cap_frames;
     H->cap_tasks = b->cap_tasks;
     H->nframes = nframes;
@@ -361,14 +374,53 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     tp.klt_warps = b->klt_warps;
     tp.klt_grid = klt_grid(b, prm->win, (int)gtype);
     tp.pyr_grid = b->pyr_grid;
+    tp.gate = 0;
     b->staged = k;
     b->next = k ^ 1;
+    b->fresh = true;
+    return VT_OK;
+}
+
+vt_status vt_batch_set_gates(vt_batch *b, const vt_gate_task *gates, int ngates, const vt_gate_params *prm) {
+    if (!b || b->staged < 0 || !b->fresh || ngates < 0 || ngates > b->cap_tasks || (ngates > 0 && !gates))
+        return VT_ERR_ARG;
+    for (int i = 0; i < ngates; ++i) {
+        const vt_gate_task &g = gates[i];
+        if (g.n < 0 || !gate_args_ok(&g.rig, prm) || (g.n > 0 && (!g.pts_l || !g.pts_r || !g.status_out)))
+            return VT_ERR_ARG;
+    }
+    const int k = b->staged;
+    uint8_t *tab = b->host[k];
+    BatchHdr *H = reinterpret_cast<BatchHdr *>(tab);
+    GTask *gt = reinterpret_cast<GTask *>(tab + H->off_gates);
+    int *p0s = reinterpret_cast<int *>(tab + H->off_gprefix);
+    long total = 0;
+    for (int i = 0; i < ngates; ++i) {
+        const vt_gate_task &g = gates[i];
+        gt[i].rig = g.rig;
+        gt[i].pts_l = reinterpret_cast<const float2 *>(g.pts_l);
+        gt[i].pts_r = reinterpret_cast<const float2 *>(g.pts_r);
+        gt[i].status_in = g.status_in;
+        gt[i].xyz = g.xyz;
+        gt[i].status_out = g.status_out;
+        gt[i].reason = g.reason;
+        gt[i].n = g.n;
+        gt[i].p0 = (int)total;
+        p0s[i] = (int)total;
+        total += g.n;
+    }
+    if (total > 0x7fffffff) return VT_ERR_ARG;
+    H->ngates = ngates;
+    H->gate_points = (int)total;
+    if (prm) H->G = *prm;
+    b->topo[k].gate = ngates > 0 ? 1 : 0;
     return VT_OK;
 }
 
 vt_status vt_batch_run(vt_batch *b, void *cuda_stream) {
     if (!b || b->staged < 0) return VT_ERR_ARG;
     const int k = b->staged;
+    b->fresh = false;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     vt_status st = enqueue(b, k, s);
     if (st != VT_OK) return st;
@@ -384,6 +436,7 @@ vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void
                              void *ev_klt1) {
     if (!b || b->staged < 0) return VT_ERR_ARG;
     const int k = b->staged;
+    b->fresh = false;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaEvent_t ev[4] = {(cudaEvent_t)ev_pyr0, (cudaEvent_t)ev_pyr1, (cudaEvent_t)ev_klt0, (cudaEvent_t)ev_klt1};
     vt_status st = enqueue(b, k, s, ev);
@@ -399,6 +452,7 @@ vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void
 vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
     if (!b || b->staged < 0) return VT_ERR_ARG;
     const int k = b->staged;
+    b->fresh = false;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (!b->exec[k] || !(b->exec_topo[k] == b->topo[k])) {
         if (b->exec[k]) {
@@ -441,7 +495,7 @@ vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_pe
     if (klt_grid_ctas) *klt_grid_ctas = b->topo[k].klt_grid;
     if (klt_warps_per_cta) *klt_warps_per_cta = b->topo[k].klt_warps;
     if (pyr_grid_ctas) *pyr_grid_ctas = b->topo[k].pyr_grid;
-    if (launches_per_run) *launches_per_run = b->staged >= 0 ? b->topo[k].maxL + 1 + 1 : 0;
+    if (launches_per_run) *launches_per_run = b->staged >= 0 ? b->topo[k].maxL + 1 + 1 + b->topo[k].gate : 0;
     return VT_OK;
 }
 

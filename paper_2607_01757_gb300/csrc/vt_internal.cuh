@@ -127,14 +127,31 @@ struct BTask {
     int n, fb, p0, levels;
 };
 
+// One stereo-gate task of a batched run: a rig and the pairs it checks.
+struct GTask {
+    vt_stereo_rig rig;
+    const float2 *pts_l, *pts_r;
+    const uint8_t *status_in;
+    float *xyz;
+    uint8_t *status_out, *reason;
+    int n, p0;
+};
+
 struct BatchHdr {
     int nframes, ntasks, total_points, maxL;
     int njobs[VT_MAX_LEVELS];   // [l < VT_MAX_LEVELS-1]: tiled pyramid launch l; [VT_MAX_LEVELS-1]: tail jobs
     int ntiles[VT_MAX_LEVELS];
     int cap_frames, cap_tasks;
     int off_frames, off_jobs, off_tasks, off_prefix;
+    int ngates, gate_points, off_gates, off_gprefix;
+    vt_gate_params G;
     KParams P;
 };
+
+// Batched stereo gate (vt_stereo.cu): every gate task of the table at dev_tab,
+// grid-stride over their pairs.
+vt_status launch_gate_batch(const uint8_t *dev_tab, int grid, cudaStream_t s);
+bool gate_args_ok(const vt_stereo_rig *rig, const vt_gate_params *prm);
 
 // Host helpers implemented in vt_pyramid.cu.
 vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,

@@ -8,7 +8,9 @@ One step of a stream with new frame(s):
 
   mono:   build cur-left; track prev-left -> cur-left (forward, backward, FB)
   stereo: build cur-left and right; track prev-left -> cur-left and
-          cur-left -> right (the cross-camera check), both with FB
+          cur-left -> right (the cross-camera check), both with FB; with a
+          gate, the left->right pairs then go through the stereo
+          triangulation gate (disparity, depth range, reprojection)
 
 All streams of a step go into one vt_batch run (persistent launches, CUDA
 graph).  The plain path issues the same work as single-pair calls, one
@@ -39,20 +41,27 @@ class StreamState:
     kp_s: object = None  # device float2 [n_max]: points tracked left -> right
     out_t: tuple = ()  # (pts, status, err)
     out_s: tuple = ()
+    rig: object = None  # vt.StereoRig of a gated stereo stream
+    gate_out: tuple = ()  # (status uint8 [n_max], xyz float [n_max, 3], reason uint8 [n_max])
     built: int = 0  # number of frames built so far (cur index = built % 2 after a build)
 
 
 class BatchedTracker:
     """Many independent camera streams tracked one step at a time."""
 
-    def __init__(self, specs, params: vt.KltParams, grad_type: int = vt.VT_GRAD_S16, device="cuda"):
+    def __init__(self, specs, params: vt.KltParams, grad_type: int = vt.VT_GRAD_S16, device="cuda",
+                 gate: vt.GateParams | None = None, rigs=None):
+        """gate / rigs: stereo triangulation gate parameters and one
+        vt.StereoRig per spec (None for mono streams); without them stereo
+        pairs are only flow-checked."""
         import torch
 
         self.torch = torch
         self.params = params
         self.grad_type = grad_type
+        self.gate = gate
         self.streams = []
-        for sp in specs:
+        for j, sp in enumerate(specs):
             s = StreamState(sp.sid, sp.w, sp.h, sp.levels, sp.stereo, sp.n_kp)
             s.pyr = [vt.vt_pyramid_create(sp.w, sp.h, sp.levels) for _ in range(2)]
             s.pyr_r = vt.vt_pyramid_create(sp.w, sp.h, sp.levels) if sp.stereo else None
@@ -65,6 +74,11 @@ class BatchedTracker:
                           torch.zeros(sp.n_kp, dtype=torch.float32, device=device))
             s.out_t = mk()
             s.out_s = mk() if sp.stereo else ()
+            if gate is not None and sp.stereo:
+                s.rig = rigs[j]
+                s.gate_out = (torch.zeros(sp.n_kp, dtype=torch.uint8, device=device),
+                              torch.zeros((sp.n_kp, 3), dtype=torch.float32, device=device),
+                              torch.zeros(sp.n_kp, dtype=torch.uint8, device=device))
             self.streams.append(s)
         nf = sum(2 if s.stereo else 1 for s in self.streams)
         self.batch_capacity = (max(1, nf), max(1, nf))
@@ -72,15 +86,16 @@ class BatchedTracker:
         self._flops = None
 
     # ------------------------------------------------------------ descriptors
-    def step_tables(self, sids, n_t, n_s, left=None, right=None, flops=None, kpt=None, kps=None):
-        """ctypes arrays (frames, tasks) of one step for streams `sids`.
+    def step_tables(self, sids, n_t, n_s, left=None, right=None, flops=None, kpt=None, kps=None, gate=True):
+        """ctypes arrays (frames, tasks) and gate tasks of one step for streams `sids`.
 
         n_t / n_s: point counts of the temporal / stereo task per stream;
         left / right: per-stream device images to build from (default: the
         stream's input slots); kpt / kps: per-stream device point arrays
         (default: the stream's point buffers); flops: optional per-stream
-        (t, s) int32 arrays."""
-        frames, tasks = [], []
+        (t, s) int32 arrays; gate: False leaves the stereo gate out of this
+        step even when the tracker has one."""
+        frames, tasks, gates = [], [], []
         for k, i in enumerate(sids):
             s = self.streams[i]
             cur = s.pyr[(s.built + 1) % 2]
@@ -100,16 +115,22 @@ class BatchedTracker:
                 pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
                 tasks.append(vt.track_task(cur, s.pyr_r, pts, s.out_s[0], s.out_s[1], s.out_s[2], fb=True, flops=fl,
                                            levels=s.levels))
+                if s.rig is not None and gate:
+                    g = s.gate_out
+                    gates.append(vt.gate_task(pts, s.out_s[0], s.rig, g[0], status_in=s.out_s[1], xyz=g[1],
+                                              reason=g[2]))
         fa = (vt.vt_frame_job * max(1, len(frames)))(*frames)
         ta = (vt.vt_track_task * max(1, len(tasks)))(*tasks)
-        return fa, len(frames), ta, len(tasks)
+        return fa, len(frames), ta, len(tasks), gates
 
     def stage(self, tables):
-        fa, nf, ta, nt = tables
+        fa, nf, ta, nt, gates = tables
         prm = self.params.c()
         code = vt._lib.vt_batch_set(self.batch, fa, nf, self.grad_type, ta, nt, C.byref(prm))
         if code != vt.VT_OK:
             raise vt.VTError("vt_batch_set", code)
+        if gates:
+            vt.vt_batch_set_gates(self.batch, gates, self.gate)
 
     def advance(self, sids):
         """After a step has been issued: the current pyramid becomes previous."""
@@ -125,7 +146,7 @@ class BatchedTracker:
             vt.vt_batch_run(self.batch, stream)
 
     # ------------------------------------------------------------- plain path
-    def plain_step(self, sids, n_t, n_s, left=None, right=None, stream=None, kpt=None, kps=None):
+    def plain_step(self, sids, n_t, n_s, left=None, right=None, stream=None, kpt=None, kps=None, gate=True):
         """The same step as single-pair calls, stream after stream."""
         import copy
 
@@ -145,8 +166,12 @@ class BatchedTracker:
             if s.stereo and n_s[k] > 0:
                 pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
                 vt.vt_klt_track_fb(cur, s.pyr_r, pts, prm, s.out_s[0], s.out_s[1], s.out_s[2], stream=stream)
+                if s.rig is not None and gate:
+                    g = s.gate_out
+                    vt.vt_stereo_gate(pts, s.out_s[0], s.rig, self.gate, g[0], status_in=s.out_s[1], xyz_out=g[1],
+                                      reason_out=g[2], stream=stream)
 
-    def plain_launches(self, sids, n_t, n_s):
+    def plain_launches(self, sids, n_t, n_s, gate=True):
         """Kernel launches of plain_step (the level-0 copy is a memcpy, not a kernel)."""
         n = 0
         for k, i in enumerate(sids):
@@ -154,6 +179,7 @@ class BatchedTracker:
             per_pyr = (s.levels - 1) + 1
             n += per_pyr * (2 if s.stereo else 1)
             n += int(n_t[k] > 0) + int(s.stereo and n_s[k] > 0)
+            n += int(s.stereo and n_s[k] > 0 and s.rig is not None and gate)
         return n
 
     def free(self):

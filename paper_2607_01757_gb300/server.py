@@ -155,11 +155,12 @@ class Server:
                 n_t.append(nt)
                 n_s.append(ns)
                 r.n_features = nt
-            tables = tr.step_tables(sids, n_t, n_s)
-            fa, nf, ta, ntk = tables
+            fa, nf, ta, ntk, gates = tr.step_tables(sids, n_t, n_s)
             code = vt._lib.vt_batch_set(slot["batch"], fa, nf, tr.grad_type, ta, ntk, vt.C.byref(self.params.c()))
             if code != vt.VT_OK:
                 raise vt.VTError("vt_batch_set", code)
+            if gates:
+                vt.vt_batch_set_gates(slot["batch"], gates, tr.gate)
             vt.vt_batch_run_graph(slot["batch"], cs)
             tr.advance(sids)
             for r, nt in zip(reqs, n_t):

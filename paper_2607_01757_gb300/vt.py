@@ -477,3 +477,78 @@ def vt_gftt_detect(g: Gftt, pyr: Pyramid, level: int, params: GfttParams, corner
     n_mask = 0 if mask is None else int(mask.shape[0])
     _check(_lib.vt_gftt_detect(g, pyr, level, C.byref(prm), _ptr(mask), n_mask, _ptr(corners_out),
                                _ptr(scores_out), _ptr(count_out), _stream(stream)), "vt_gftt_detect")
+
+
+# ------------------------------------------------------------------ stereo gate
+class vt_stereo_rig(C.Structure):
+    _fields_ = [("kl", C.c_double * 4), ("kr", C.c_double * 4), ("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class vt_gate_params(C.Structure):
+    _fields_ = [("min_disp", C.c_double), ("z_min", C.c_double), ("z_max", C.c_double),
+                ("max_reproj", C.c_double)]
+
+
+_sig("vt_stereo_gate", i32, [vp, vp, vp, i32, C.POINTER(vt_stereo_rig), C.POINTER(vt_gate_params), vp, vp, vp,
+                             vp])
+
+VT_LOST_DISP, VT_LOST_DEPTH, VT_LOST_REPROJ = 5, 6, 7
+
+
+@dataclass
+class StereoRig:
+    """Pinhole intrinsics (fx, fy, cx, cy) of both cameras and the left-to-right
+    extrinsics X_R = R X_L + t (R row-major, t in metres)."""
+    kl: tuple
+    kr: tuple
+    R: tuple = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+    t: tuple = (0.0, 0.0, 0.0)
+
+    def c(self) -> vt_stereo_rig:
+        import numpy as np
+
+        def flat(v, n):
+            a = np.asarray(v, np.float64).ravel()
+            if a.size != n:
+                raise ValueError(f"expected {n} values, got {a.size}")
+            return (C.c_double * n)(*a.tolist())
+
+        return vt_stereo_rig(flat(self.kl, 4), flat(self.kr, 4), flat(self.R, 9), flat(self.t, 3))
+
+
+@dataclass
+class GateParams:
+    min_disp: float = 1.0
+    z_min: float = 0.1
+    z_max: float = 50.0
+    max_reproj: float = 1.5
+
+    def c(self) -> vt_gate_params:
+        return vt_gate_params(self.min_disp, self.z_min, self.z_max, self.max_reproj)
+
+
+def vt_stereo_gate(pts_l, pts_r, rig: StereoRig, params: GateParams, status_out, status_in=None, xyz_out=None,
+                   reason_out=None, stream=None) -> None:
+    n = int(pts_l.shape[0])
+    r, p = rig.c(), params.c()
+    _check(_lib.vt_stereo_gate(_ptr(pts_l), _ptr(pts_r), _ptr(status_in), n, C.byref(r), C.byref(p), _ptr(xyz_out),
+                               _ptr(status_out), _ptr(reason_out), _stream(stream)), "vt_stereo_gate")
+
+
+class vt_gate_task(C.Structure):
+    _fields_ = [("pts_l", vp), ("pts_r", vp), ("status_in", vp), ("n", i32), ("rig", vt_stereo_rig), ("xyz", vp),
+                ("status_out", vp), ("reason", vp)]
+
+
+_sig("vt_batch_set_gates", i32, [vp, C.POINTER(vt_gate_task), i32, C.POINTER(vt_gate_params)])
+
+
+def gate_task(pts_l, pts_r, rig: StereoRig, status_out, status_in=None, xyz=None, reason=None) -> vt_gate_task:
+    return vt_gate_task(_ptr(pts_l), _ptr(pts_r), _ptr(status_in), int(pts_l.shape[0]), rig.c(), _ptr(xyz),
+                        _ptr(status_out), _ptr(reason))
+
+
+def vt_batch_set_gates(b: Batch, gates, params: GateParams) -> None:
+    arr = (vt_gate_task * max(1, len(gates)))(*gates)
+    prm = params.c()
+    _check(_lib.vt_batch_set_gates(b, arr, len(gates), C.byref(prm)), "vt_batch_set_gates")

@@ -24,6 +24,7 @@ from .scenes import (
     StreamSpec,
     make_stream_mix,
     render_stream_frames,
+    stream_rig,
 )
 
 __all__ = [
@@ -39,4 +40,5 @@ __all__ = [
     "StreamSpec",
     "make_stream_mix",
     "render_stream_frames",
+    "stream_rig",
 ]

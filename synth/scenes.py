@@ -257,6 +257,18 @@ class StreamFrames:
     kps: list  # keypoints on each left frame
 
 
+def stream_rig(spec: StreamSpec, baseline: float = 0.11):
+    """Calibration of a stream's (rectified) stereo rig as plain numbers:
+    pinhole (f, f, cx, cy) for both cameras with f = 460 px scaled by the
+    width from 752 px and the principal point at the image centre, identity
+    rotation and the right camera `baseline` metres along +x (X_R = X_L + t,
+    t = (-baseline, 0, 0)).  The constant disparity d of render_stream_frames
+    is then a fronto-parallel plane at depth f * baseline / d."""
+    f = 460.0 * spec.w / 752.0
+    k = (f, f, (spec.w - 1) / 2.0, (spec.h - 1) / 2.0)
+    return k, k, (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0), (-baseline, 0.0, 0.0)
+
+
 def render_stream_frames(spec: StreamSpec, n_frames: int = 4, max_shift: float = 6.0,
                          max_rot_deg: float = 0.5) -> StreamFrames:
     """Frames k = 0..n_frames-1 of one stream: texture under a random walk of

@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,3 +72,32 @@ def test_supported_windows_match_header(win):
         m = re.search(r"#define VT_SUPPORTED_WINDOWS \{([^}]*)\}", f.read())
     assert win in [int(t) for t in m.group(1).split(",")]
     assert win in vt.SUPPORTED_WINDOWS
+
+
+def test_stereo_gate_argument_errors_need_no_device():
+    import paper_2607_01757_gb300 as vt
+
+    f = vt.vt_stereo_gate
+    rig = vt.StereoRig((460.0, 460.0, 375.5, 239.5), (460.0, 460.0, 375.5, 239.5), t=(-0.11, 0.0, 0.0))
+    prm = vt.GateParams()
+    from paper_2607_01757_gb300.vt import _lib as lib
+
+    one = C.c_void_p(16)
+    call = lambda n, r, p, pl=one, st=one: lib.vt_stereo_gate(pl, one, None, n, C.byref(r), C.byref(p), None, st,
+                                                            None, None)  # noqa: E731
+    assert call(0, rig.c(), prm.c()) == vt.VT_OK  # n == 0 launches nothing
+    assert call(-1, rig.c(), prm.c()) == vt.VT_ERR_ARG
+    assert call(5, rig.c(), prm.c(), pl=None) == vt.VT_ERR_ARG
+    assert call(5, rig.c(), prm.c(), st=None) == vt.VT_ERR_ARG
+    bad = rig.c()
+    bad.kl[0] = 0.0
+    assert call(5, bad, prm.c()) == vt.VT_ERR_ARG
+    bad = rig.c()
+    bad.R[4] = float("nan")
+    assert call(5, bad, prm.c()) == vt.VT_ERR_ARG
+    for p in (vt.GateParams(min_disp=-1.0), vt.GateParams(z_min=5.0, z_max=1.0), vt.GateParams(max_reproj=-0.1),
+              vt.GateParams(z_min=float("nan"))):
+        assert call(5, rig.c(), p.c()) == vt.VT_ERR_ARG
+    with pytest.raises(vt.VTError):
+        f(np.zeros((3, 2), np.float32), np.zeros((3, 2), np.float32), rig, vt.GateParams(min_disp=-2.0),
+          np.zeros(3, np.uint8), stream=0)
