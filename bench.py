@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-gftt", action="store_true")
     ap.add_argument("--no-gate", action="store_true")
+    ap.add_argument("--grad", default="s16", choices=["s16", "f16", "none"],
+                    help="gradient storage: int16 / half planes, or none (computed inside the tracker)")
     ap.add_argument("--served-streams", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=10000)
     ap.add_argument("--served-budget-gb", type=float, default=20.0)
@@ -188,7 +190,8 @@ def run_native(a, rank, world, local_rank):
     prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, fb_thr=0.5)
     gprm = vt.GateParams(min_disp=1.0, z_min=0.1, z_max=50.0, max_reproj=1.5)
     rigs = [vt.StereoRig(*synth.stream_rig(sp)) if sp.stereo else None for sp in specs]
-    tr = BatchedTracker(specs, prm, gate=gprm, rigs=rigs)
+    grad_type = {"s16": vt.VT_GRAD_S16, "f16": vt.VT_GRAD_F16, "none": vt.VT_GRAD_NONE}[a.grad]
+    tr = BatchedTracker(specs, prm, grad_type=grad_type, gate=gprm, rigs=rigs)
     S = len(specs)
     sids = list(range(S))
     # device frame store: frames and keypoints of every stream
@@ -339,7 +342,7 @@ def run_native(a, rank, world, local_rank):
             w, h = (w + 1) // 2, (h + 1) // 2
         b = dims[0][0] * dims[0][1]  # level-0 copy
         for l, (lw, lh) in enumerate(dims):
-            b += lw * lh + 4 * lw * lh
+            b += lw * lh + (0 if grad_type == vt.VT_GRAD_NONE else 4) * lw * lh
             if l + 1 < len(dims):
                 b += dims[l + 1][0] * dims[l + 1][1]
         pyr_bytes += b * (2 if s.stereo else 1)
@@ -350,7 +353,7 @@ def run_native(a, rank, world, local_rank):
             peaks = json.load(f)
     except OSError:
         pass
-    default_wl = (a.streams, a.frames, a.seed) == (32, 4, 4) and world == 1
+    default_wl = (a.streams, a.frames, a.seed, a.grad) == (32, 4, 4, "s16") and world == 1
     traffic = NCU_TRAFFIC_BYTES if default_wl else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
@@ -499,6 +502,8 @@ def run_native(a, rank, world, local_rank):
             "stereo_streams": sum(1 for s in specs if s.stereo),
             "features_per_step": feats // a.steps,
             "frames_per_stream": F,
+            "gradients": {"s16": "stored int16 Scharr planes", "f16": "stored half Scharr planes",
+                          "none": "computed inside the tracker (bit-identical to int16)"}[a.grad],
             "win": prm.win, "levels": "per stream (4-6)", "max_iters": prm.max_iters, "eps": prm.eps,
             "fb_thr": prm.fb_thr,
             "l2": "flushed between steps (256 MB write outside the per-step CUDA events)",

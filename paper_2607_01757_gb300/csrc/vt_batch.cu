@@ -92,6 +92,8 @@ static KltBatchKernel klt_batch_fn(int win) {
 
 static KltBatchKernel klt_batch_kernel(int win, int gtype, int warps) {
     if (gtype == VT_GRAD_F16) return warps == 8 ? klt_batch_fn<VT_GRAD_F16, 8>(win) : klt_batch_fn<VT_GRAD_F16, 4>(win);
+    if (gtype == VT_GRAD_NONE)
+        return warps == 8 ? klt_batch_fn<VT_GRAD_NONE, 8>(win) : klt_batch_fn<VT_GRAD_NONE, 4>(win);
     return warps == 8 ? klt_batch_fn<VT_GRAD_S16, 8>(win) : klt_batch_fn<VT_GRAD_S16, 4>(win);
 }
 
@@ -250,7 +252,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     if (!b || !prm || nframes < 0 || ntasks < 0 || nframes > b->cap_frames || ntasks > b->cap_tasks)
         return VT_ERR_ARG;
     if ((nframes > 0 && !frames) || (ntasks > 0 && !tasks)) return VT_ERR_ARG;
-    if (gtype != VT_GRAD_S16 && gtype != VT_GRAD_F16) return VT_ERR_ARG;
+    if (gtype != VT_GRAD_S16 && gtype != VT_GRAD_F16 && gtype != VT_GRAD_NONE) return VT_ERR_ARG;
     if (!window_supported(prm->win) || prm->levels < 0 || prm->levels > VT_MAX_LEVELS || prm->max_iters < 1 ||
         !(prm->eps >= 0.f) || !(prm->min_eig >= 0.f) || !(prm->fb_thr >= 0.f))
         return VT_ERR_ARG;
@@ -556,8 +558,8 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
         !(prm->eps >= 0.f) || !(prm->min_eig >= 0.f) || !(prm->fb_thr >= 0.f))
         return VT_ERR_ARG;
     if (ntasks == 0) return VT_OK;
-    const int gtype = tasks[0].prev ? tasks[0].prev->gtype : VT_GRAD_NONE;
-    if (gtype != VT_GRAD_S16 && gtype != VT_GRAD_F16) return VT_ERR_ARG;
+    if (!tasks[0].prev) return VT_ERR_ARG;
+    const int gtype = tasks[0].prev->gtype;  // VT_GRAD_NONE: gradients computed in the tracker
     long total = 0;
     for (int t = 0; t < ntasks; ++t) {
         const vt_track_task &tk = tasks[t];

@@ -98,7 +98,6 @@ static vt_status track_common(const vt_pyramid *prev, const vt_pyramid *cur, con
     if (prm->levels < 1 || prm->levels > prev->levels || prm->levels > cur->levels) return VT_ERR_ARG;
     if (prm->max_iters < 1 || !(prm->eps >= 0.f) || !(prm->min_eig >= 0.f)) return VT_ERR_ARG;
     if (fb && !(prm->fb_thr >= 0.f)) return VT_ERR_ARG;
-    if (prev->gtype == VT_GRAD_NONE) return VT_ERR_ARG;
     if (fb && cur->gtype != prev->gtype) return VT_ERR_ARG;
     if (n == 0) return VT_OK;
     KltArgs A;
@@ -124,6 +123,8 @@ static vt_status track_common(const vt_pyramid *prev, const vt_pyramid *cur, con
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (prev->gtype == VT_GRAD_F16)
         return fb ? dispatch_win<VT_GRAD_F16, true>(A, s) : dispatch_win<VT_GRAD_F16, false>(A, s);
+    if (prev->gtype == VT_GRAD_NONE)  // gradients computed in the tracker, as int16 Scharr
+        return fb ? dispatch_win<VT_GRAD_NONE, true>(A, s) : dispatch_win<VT_GRAD_NONE, false>(A, s);
     return fb ? dispatch_win<VT_GRAD_S16, true>(A, s) : dispatch_win<VT_GRAD_S16, false>(A, s);
 }
 

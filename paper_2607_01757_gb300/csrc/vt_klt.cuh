@@ -86,9 +86,10 @@ __device__ __forceinline__ void unpack_grad(uint32_t v, float &gx, float &gy) {
     }
 }
 
-// Scale from the stored gradient unit to grey levels per pixel.
+// Scale from the stored gradient unit to grey levels per pixel (gradients
+// computed on the fly, VT_GRAD_NONE, are raw Scharr like VT_GRAD_S16).
 template <int GT>
-__device__ __forceinline__ constexpr float grad_unit() { return GT == VT_GRAD_S16 ? 0.03125f : 1.0f; }
+__device__ __forceinline__ constexpr float grad_unit() { return GT == VT_GRAD_F16 ? 1.0f : 0.03125f; }
 
 // 2^-l exactly.
 __device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
@@ -102,11 +103,98 @@ struct KSmem {
     uint8_t j[(WIN + 1) * JS];
 };
 
+// Template of a level without stored gradients: lane c computes the raw
+// Scharr response of window column c from the level image itself -- the
+// integers the pyramid kernels would have stored (reflect-101 neighbours of
+// the replicate-clamped pixel) -- then samples exactly as load_template does,
+// so the result is bit-identical to tracking on stored int16 gradients.
+//
+// Per image row y the lane forms d(y) = I(y, x+1) - I(y, x-1) and
+// s(y) = 3 I(y, x-1) + 10 I(y, x) + 3 I(y, x+1); the gradient of row y is
+// dx = 3 d(y-1) + 10 d(y) + 3 d(y+1), dy = s(y+1) - s(y-1).  The clamped rows
+// R(k) = clamp(y0 + k) are read once each (a rolling window): for an
+// interior row R(r) its neighbours are R(r-1) and R(r+1); a row at the
+// image's first or last line takes its reflected neighbour (row 1 or h-2)
+// on both sides instead.
+template <int WIN>
+__device__ __forceinline__ void load_template_otf(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
+                                                  float (&GX)[WIN], float (&GY)[WIN]) {
+    constexpr int HW = WIN / 2;
+    const float fx = floorf(ux), fy = floorf(uy);
+    const float ax = ux - fx, ay = uy - fy;
+    const int x0 = (int)fx - HW, y0 = (int)fy - HW;
+    const bool ld = lane <= WIN;
+    const int q = clampi(x0 + lane, 0, L.w - 1);
+    const int qm = refl101(q - 1, L.w), qp = refl101(q + 1, L.w);
+    const int hm1 = L.h - 1;
+    auto terms = [&](int y, int &d, int &sm, int &c) {
+        const uint8_t *rp = L.img + (size_t)y * L.pitch;
+        int a = 0, b = 0, e = 0;
+        if (ld) {
+            a = __ldg(rp + qm);
+            b = __ldg(rp + q);
+            e = __ldg(rp + qp);
+        }
+        d = e - a;
+        sm = 3 * (a + e) + 10 * b;
+        c = b;
+    };
+    // reflected neighbours of the first and last image rows (used only when
+    // the window reaches them)
+    int dt = 0, st = 0, db = 0, sb = 0, unused;
+    if (y0 <= 0 || hm1 == 0) terms(refl101(-1, L.h), dt, st, unused);
+    if (y0 + WIN >= hm1) terms(refl101(L.h, L.h), db, sb, unused);
+    int dm, sm_m, cm, d0, s0, c0;
+    terms(clampi(y0 - 1, 0, hm1), dm, sm_m, cm);
+    terms(clampi(y0, 0, hm1), d0, s0, c0);
+    float pi = 0.f, pgx = 0.f, pgy = 0.f;
+#pragma unroll
+    for (int r = 0; r <= WIN; ++r) {
+        const int yc = clampi(y0 + r, 0, hm1);
+        int dp, sp, cp;
+        terms(clampi(y0 + r + 1, 0, hm1), dp, sp, cp);
+        // first / last image row: the reflected neighbour on both sides
+        const bool top = yc == 0, bot = yc == hm1;
+        const int du = top ? dt : (bot ? db : dm), su = top ? st : (bot ? sb : sm_m);
+        const int dd = top ? dt : (bot ? db : dp), sd = top ? st : (bot ? sb : sp);
+        const float gx = (float)(3 * (du + dd) + 10 * d0);
+        const float gy = (float)(sd - su);
+        const float mv = magic_u8((uint32_t)c0);
+        dm = d0;
+        sm_m = s0;
+        d0 = dp;
+        s0 = sp;
+        c0 = cp;
+        const float mvr = __shfl_down_sync(kFull, mv, 1);
+        const float gxr = __shfl_down_sync(kFull, gx, 1);
+        const float gyr = __shfl_down_sync(kFull, gy, 1);
+        const float hi = fmaf(ax, mvr - mv, mv - kMagic);
+        const float hgx = fmaf(ax, gxr - gx, gx);
+        const float hgy = fmaf(ax, gyr - gy, gy);
+        if (r > 0) {
+            T[r - 1] = fmaf(ay, hi - pi, pi);
+            GX[r - 1] = fmaf(ay, hgx - pgx, pgx);
+            GY[r - 1] = fmaf(ay, hgy - pgy, pgy);
+        }
+        pi = hi;
+        pgx = hgx;
+        pgy = hgy;
+    }
+    if (lane >= WIN) {
+#pragma unroll
+        for (int r = 0; r < WIN; ++r) T[r] = GX[r] = GY[r] = 0.f;
+    }
+}
+
 // Sample the template of level `L` around (ux, uy): lane c ends with column
 // c of T and of its gradients (zero for c >= WIN).
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
                                               float (&GX)[WIN], float (&GY)[WIN]) {
+    if constexpr (GT == VT_GRAD_NONE) {
+        load_template_otf<WIN>(L, ux, uy, lane, T, GX, GY);
+        return;
+    }
     constexpr int HW = WIN / 2;
     const float fx = floorf(ux), fy = floorf(uy);
     const float ax = ux - fx, ay = uy - fy;

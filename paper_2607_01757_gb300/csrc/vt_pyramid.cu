@@ -148,7 +148,7 @@ __device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int
         uint32_t *out = reinterpret_cast<uint32_t *>(&s_v[r][0]) + 2 * j;
         *reinterpret_cast<uint2 *>(out) = make_uint2(__byte_perm(sl, sh, 0x5410), __byte_perm(sl, sh, 0x7632));
     }
-    if (GRAD) {
+    if constexpr (GRAD) {
         const int g = threadIdx.x & 31, rg = threadIdx.x >> 5;
         const int xr = 4 * g, x = 2 * ox0 + xr;
         int t0[6], t1[6], t2[6];
@@ -305,7 +305,8 @@ __device__ __forceinline__ int find_job(const BLvlJob *jobs, int n, int t) {
 }
 
 // Launch `l` (< VT_MAX_LEVELS - 1): level l -> l+1 plus the Scharr planes of
-// level l for every frame of the batch whose tail starts above l.  Level 0
+// level l for every frame of the batch whose tail starts above l (no Scharr
+// planes for GT = VT_GRAD_NONE: the tracker computes gradients itself).  Level 0
 // reads the caller's image and writes the pyramid's level-0 copy from the
 // same tile.  The job list is first copied to shared memory so the per-tile
 // job search does not chain global loads.
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, in
         int tx, ty;
         locate(t, r, fr, tx, ty);
         const Level src = fr.lv[l], dst = fr.lv[l + 1];
-        pyr_tile<true, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad, src.gpitch,
-                           l == 0 ? src.img : nullptr, src.pitch, tx, ty, s_in, s_v);
+        pyr_tile<GT != VT_GRAD_NONE, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad,
+                                         src.gpitch, l == 0 ? src.img : nullptr, src.pitch, tx, ty, s_in, s_v);
         __syncthreads();
     }
 }
@@ -485,14 +486,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
             __syncthreads();
             const int band = (Lc.h + parts - 1) / parts;
             const int y0 = part * band, y1 = min(Lc.h, y0 + band);
-            tail_scharr<GT>(cur, Lc.pitch, Lc.w, Lc.h, y0, y1, Lc.grad, Lc.gpitch);
+            if constexpr (GT != VT_GRAD_NONE) tail_scharr<GT>(cur, Lc.pitch, Lc.w, Lc.h, y0, y1, Lc.grad, Lc.gpitch);
             if (part == 0) {
                 int stride = Lc.pitch;
                 for (int l = c; l + 1 < fr.levels; ++l) {
                     const Level L = fr.lv[l], N = fr.lv[l + 1];
                     tail_pyrdown(cur, stride, L.w, L.h, nxt, N.img, N.pitch);
                     __syncthreads();
-                    tail_scharr<GT>(nxt, N.w, N.w, N.h, 0, N.h, N.grad, N.gpitch);
+                    if constexpr (GT != VT_GRAD_NONE) tail_scharr<GT>(nxt, N.w, N.w, N.h, 0, N.h, N.grad, N.gpitch);
                     uint8_t *t = cur;
                     cur = nxt;
                     nxt = t;
@@ -500,13 +501,19 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
                 }
             }
         } else if (part == 0) {
-            uint8_t (*s_in)[SC_IW] = reinterpret_cast<uint8_t (*)[SC_IW]>(tail_smem);
-            int tiles_x;
-            const int tiles = scharr_tiles(Lc.w, Lc.h, tiles_x);
-            for (int t = 0; t < tiles; ++t) {
-                const int ty = t / tiles_x, tx = t - ty * tiles_x;
-                scharr_tile<GT>(src, Lc.w, Lc.h, sp, c == 0 ? fr.vec_ok != 0 : true, Lc.grad, Lc.gpitch,
-                                c == 0 ? Lc.img : nullptr, Lc.pitch, tx, ty, s_in);
+            if constexpr (GT != VT_GRAD_NONE) {
+                uint8_t (*s_in)[SC_IW] = reinterpret_cast<uint8_t (*)[SC_IW]>(tail_smem);
+                int tiles_x;
+                const int tiles = scharr_tiles(Lc.w, Lc.h, tiles_x);
+                for (int t = 0; t < tiles; ++t) {
+                    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+                    scharr_tile<GT>(src, Lc.w, Lc.h, sp, c == 0 ? fr.vec_ok != 0 : true, Lc.grad, Lc.gpitch,
+                                    c == 0 ? Lc.img : nullptr, Lc.pitch, tx, ty, s_in);
+                }
+            } else if (c == 0) {  // no gradients: only the level-0 copy of a large one-level pyramid
+                const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                for (int y = threadIdx.x >> 5; y < Lc.h; y += nw)
+                    for (int x = lane; x < Lc.w; x += 32) Lc.img[(size_t)y * Lc.pitch + x] = src[(size_t)y * sp + x];
             }
         }
         __syncthreads();
@@ -530,16 +537,21 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
     if (!attr) {
         cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_S16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
         cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
+        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
         attr = true;
     }
     for (int l = 0; l < tiled_launches; ++l) {
         if (gtype == VT_GRAD_F16)
             k_pyr_batch<VT_GRAD_F16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
+        else if (gtype == VT_GRAD_NONE)
+            k_pyr_batch<VT_GRAD_NONE><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
         else
             k_pyr_batch<VT_GRAD_S16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
     }
     if (gtype == VT_GRAD_F16)
         k_pyr_tail<VT_GRAD_F16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
+    else if (gtype == VT_GRAD_NONE)
+        k_pyr_tail<VT_GRAD_NONE><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
     else
         k_pyr_tail<VT_GRAD_S16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;

@@ -28,32 +28,48 @@ struct GateArgs {
     vt_gate_params prm;
 };
 
+// One Jacobi rotation in the (P, Q) plane of the symmetric M (upper
+// triangle M[i][j], i < j, and the diagonal are kept), accumulating V.
+//
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the angle is
+// found in FP32 (tan t, the smaller root of t^2 + 2 tau t - 1 = 0,
+// tau = (M_QQ - M_PP) / 2 M_PQ) and only made exactly orthogonal in FP64:
+// c = 1 / sqrt(1 + t^2) by two Newton steps from the FP32 estimate, s = t c,
+// so c^2 + s^2 = 1 to FP64 rounding.  An approximate angle leaves a small
+// M_PQ behind for the next sweep; the update itself is the full similarity
+// J^T M J in FP64, so the eigenvectors keep FP64 accuracy.
 template <int P, int Q>
 __device__ __forceinline__ void jacobi_rotate(double (&M)[4][4], double (&V)[4][4]) {
     const double apq = M[P][Q];
     if (apq == 0.0) return;
-    // angle that zeroes M[P][Q]: tan = t, the smaller root of t^2 + 2 tau t - 1 = 0
-    const double tau = (M[Q][Q] - M[P][P]) / (2.0 * apq);
-    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(tau * tau + 1.0));
-    const double c = 1.0 / sqrt(t * t + 1.0);
+    const float tau = (float)(M[Q][Q] - M[P][P]) / (2.0f * (float)apq);
+    const float tf = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    if (tf == 0.0f) return;  // |M_PQ| negligible against |M_QQ - M_PP|
+    const double t = tf;
+    const double x = fma(t, t, 1.0);
+    double c = (double)rsqrtf((float)x);
+    c = c * fma(-0.5 * x, c * c, 1.5);
+    c = c * fma(-0.5 * x, c * c, 1.5);
     const double s = t * c;
+    const double cc = c * c, ss = s * s, cs = c * s;
+    const double app = M[P][P], aqq = M[Q][Q];
+    M[P][P] = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
+    M[Q][Q] = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
+    M[P][Q] = fma(cc - ss, apq, cs * (app - aqq));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {  // columns P, Q of M J
-        const double a = M[k][P], b = M[k][Q];
-        M[k][P] = c * a - s * b;
-        M[k][Q] = s * a + c * b;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {  // rows P, Q of J^T (M J)
-        const double a = M[P][k], b = M[Q][k];
-        M[P][k] = c * a - s * b;
-        M[Q][k] = s * a + c * b;
+    for (int k = 0; k < 4; ++k) {  // the other rows / columns of J^T M J
+        if (k == P || k == Q) continue;
+        double &mkp = k < P ? M[k][P] : M[P][k];
+        double &mkq = k < Q ? M[k][Q] : M[Q][k];
+        const double a = mkp, b = mkq;
+        mkp = fma(c, a, -s * b);
+        mkq = fma(s, a, c * b);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {  // eigenvectors accumulate as columns of V J
         const double a = V[k][P], b = V[k][Q];
-        V[k][P] = c * a - s * b;
-        V[k][Q] = s * a + c * b;
+        V[k][P] = fma(c, a, -s * b);
+        V[k][Q] = fma(s, a, c * b);
     }
 }
 
@@ -65,8 +81,10 @@ __device__ __forceinline__ void dlt_null_vector(const double (&A)[4][4], double 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             double s = 0.0;
+            if (j >= i) {  // upper triangle only
 #pragma unroll
-            for (int r = 0; r < 4; ++r) s += A[r][i] * A[r][j];
+                for (int r = 0; r < 4; ++r) s += A[r][i] * A[r][j];
+            }
             M[i][j] = s;
             V[i][j] = i == j ? 1.0 : 0.0;
         }

@@ -155,11 +155,9 @@ class BatchedTracker:
             prm = copy.copy(self.params)
             prm.levels = s.levels
             prev, cur = s.pyr[s.built % 2], s.pyr[(s.built + 1) % 2]
-            vt.vt_pyramid_build_grad(left[k] if left is not None else s.in_left, s.levels, self.grad_type, stream,
-                                     out=cur)
+            self._build(left[k] if left is not None else s.in_left, s.levels, stream, cur)
             if s.stereo:
-                vt.vt_pyramid_build_grad(right[k] if right is not None else s.in_right, s.levels, self.grad_type,
-                                         stream, out=s.pyr_r)
+                self._build(right[k] if right is not None else s.in_right, s.levels, stream, s.pyr_r)
             if n_t[k] > 0:
                 pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
                 vt.vt_klt_track_fb(prev, cur, pts, prm, s.out_t[0], s.out_t[1], s.out_t[2], stream=stream)
@@ -171,12 +169,18 @@ class BatchedTracker:
                     vt.vt_stereo_gate(pts, s.out_s[0], s.rig, self.gate, g[0], status_in=s.out_s[1], xyz_out=g[1],
                                       reason_out=g[2], stream=stream)
 
+    def _build(self, img, levels, stream, out):
+        if self.grad_type == vt.VT_GRAD_NONE:  # the tracker computes gradients itself
+            vt.vt_pyramid_build(img, levels, stream, out=out)
+        else:
+            vt.vt_pyramid_build_grad(img, levels, self.grad_type, stream, out=out)
+
     def plain_launches(self, sids, n_t, n_s, gate=True):
         """Kernel launches of plain_step (the level-0 copy is a memcpy, not a kernel)."""
         n = 0
         for k, i in enumerate(sids):
             s = self.streams[i]
-            per_pyr = (s.levels - 1) + 1
+            per_pyr = (s.levels - 1) + (0 if self.grad_type == vt.VT_GRAD_NONE else 1)
             n += per_pyr * (2 if s.stereo else 1)
             n += int(n_t[k] > 0) + int(s.stereo and n_s[k] > 0)
             n += int(s.stereo and n_s[k] > 0 and s.rig is not None and gate)

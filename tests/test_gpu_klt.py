@@ -202,8 +202,8 @@ def test_argument_errors():
     p = vt.vt_pyramid_build(img, 3)
     e = torch.zeros((4, 2), device="cuda")
     s = torch.zeros(4, dtype=torch.uint8, device="cuda")
-    with pytest.raises(vt.VTError):  # no gradients yet
-        vt.vt_klt_track_ex(p, p, e, vt.KltParams(levels=3), e, s)
+    # no stored gradients: the tracker computes them (no error)
+    vt.vt_klt_track_ex(p, p, e, vt.KltParams(levels=3), e, s)
     vt.vt_gradients(p)
     for bad in (vt.KltParams(levels=4), vt.KltParams(levels=3, win=20), vt.KltParams(levels=3, win=11),
                 vt.KltParams(levels=3, max_iters=0), vt.KltParams(levels=3, eps=-1.0)):
