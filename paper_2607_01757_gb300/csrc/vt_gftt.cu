@@ -10,25 +10,34 @@
 //                     local maximum of its (2nms+1)^2 neighbourhood (ties to
 //                     the smaller index), far enough from every mask point:
 //                     appended as a 64-bit key (score bits, ~index).
-//   K6c k_gftt_sort   one CTA, bitonic sort of the keys, descending.
-//   K6d k_gftt_greedy one warp: candidates in priority order, 32 at a time;
-//                     each lane checks its candidate against the kept corners
-//                     through a cell grid in shared memory (cells at least
-//                     min_dist wide, linked lists), then the 32 are resolved
-//                     in order by warp votes; stops at max_corners.
+//   K6c cell grid     counting sort of the candidates into cells at least
+//                     min_dist wide (count, one-CTA scan, scatter).
+//   K6d k_gftt_select the greedy min-distance selection in priority order,
+//                     resolved in parallel rounds over the cell grid
+//                     (cooperative launch, grid-wide barrier per round).
+//   K6e k_gftt_output the kept candidates sorted (shared-memory bitonic sort)
+//                     and the first max_corners written out.
 // Every decision is taken on the same FP32 values the oracle computes, so the
 // corner list is exact.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 #include <cstdlib>
 
 #include "vt_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace vt {
 
 constexpr int GF_BX = 32, GF_BY = 8;
 constexpr int GF_SORT_THREADS = 1024;
-constexpr int GF_MAX_CELLS = 24576;     // cell-grid heads in shared memory (int16)
+constexpr int GF_SCAN_THREADS = 1024;
+constexpr int GF_MIS_THREADS = 256;
+constexpr int GF_SMEM_SORT = 16384;  // kept keys sorted in shared memory (128 KB)
 constexpr int GF_MAX_CORNERS = 8192;
+constexpr int GF_GRID_THREADS = 256;
+enum : uint8_t { GF_UNDECIDED = 0, GF_KEPT = 1, GF_REJECTED = 2 };
 
 __device__ __forceinline__ float gftt_score(long long a, long long b, long long c) {
     const float fa = (float)a, fb = (float)b, fc = (float)c;
@@ -104,93 +113,166 @@ __global__ void k_gftt_cand(const float *score, int w, int h, const unsigned *ma
         keys[slot] = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)(0xffffffffu - (unsigned)idx);
 }
 
-// Bitonic sort (descending) of the first `n` keys, padded with zeros to a power of two.
-__global__ void __launch_bounds__(GF_SORT_THREADS) k_gftt_sort(unsigned long long *keys, const int *count, int cap) {
+__device__ __forceinline__ unsigned key_index(unsigned long long k) { return 0xffffffffu - (unsigned)(k & 0xffffffffu); }
+
+// Candidates into a grid of cells at least min_dist wide (a counting sort:
+// count, scan, scatter), so every pair closer than min_dist lies in
+// neighbouring cells.
+__global__ void k_gftt_cell_count(const unsigned long long *keys, const int *count, int cap, int w, int cell,
+                                  int cells_x, int *cell_count, int *rank) {
     const int n = min(*count, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned idx = key_index(keys[i]);
+        const int x = (int)(idx % (unsigned)w), y = (int)(idx / (unsigned)w);
+        rank[i] = atomicAdd(&cell_count[(y / cell) * cells_x + x / cell], 1);
+    }
+}
+
+// Exclusive scan of cell_count[0..ncell) into cell_start[0..ncell] (one CTA).
+__global__ void __launch_bounds__(GF_SCAN_THREADS) k_gftt_cell_scan(const int *cell_count, int ncell,
+                                                                      int *cell_start) {
+    __shared__ int part[GF_SCAN_THREADS];
+    const int per = (ncell + GF_SCAN_THREADS - 1) / GF_SCAN_THREADS;
+    const int b = threadIdx.x * per, e = min(ncell, b + per);
+    int sum = 0;
+    for (int i = b; i < e; ++i) sum += cell_count[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < GF_SCAN_THREADS; o <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int i = b; i < e; ++i) {
+        cell_start[i] = run;
+        run += cell_count[i];
+    }
+    if (threadIdx.x == GF_SCAN_THREADS - 1) cell_start[ncell] = part[GF_SCAN_THREADS - 1];
+}
+
+__global__ void k_gftt_cell_scatter(const unsigned long long *keys, const int *count, int cap, int w, int cell,
+                                    int cells_x, const int *cell_start, const int *rank, unsigned long long *skeys,
+                                    uint8_t *state) {
+    const int n = min(*count, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const unsigned idx = key_index(k);
+        const int x = (int)(idx % (unsigned)w), y = (int)(idx / (unsigned)w);
+        const int pos = cell_start[(y / cell) * cells_x + x / cell] + rank[i];
+        skeys[pos] = k;
+        state[pos] = GF_UNDECIDED;
+    }
+}
+
+// The greedy min-distance selection, resolved in parallel rounds.  In
+// priority order, a candidate is kept when no kept candidate lies closer than
+// min_dist; its fate therefore depends only on the higher-priority
+// candidates within min_dist.  Each round decides every undecided candidate
+// whose closer higher-priority neighbours are all decided: rejected if one of
+// them is kept, kept otherwise.  States only move from undecided to final,
+// and a final state is the sequential greedy's, so reading a neighbour that
+// another thread finalises in the same round is harmless.  The highest-
+// priority undecided candidate is always decided, so the rounds end (in
+// practice after a few dozen).  Rounds are separated by grid-wide barriers
+// (cooperative launch); the kept candidates are then appended to `kept`.
+__global__ void __launch_bounds__(GF_MIS_THREADS) k_gftt_select(const unsigned long long *skeys, const int *count,
+                                                                 int cap, int w, int cell, int cells_x, int cells_y,
+                                                                 const int *cell_start, uint8_t *state, int *und,
+                                                                 long long d2, unsigned long long *kept,
+                                                                 int *kept_count) {
+    cg::grid_group grid = cg::this_grid();
+    const int n = min(*count, cap);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    volatile uint8_t *vs = state;
+    for (int r = 0;; ++r) {
+        if (tid == 0) und[(r + 1) % 3] = 0;  // the slot round r+1 counts into (last read before round r)
+        int mine = 0;
+        for (int i = tid; i < n; i += nth) {
+            if (vs[i] != GF_UNDECIDED) continue;
+            const unsigned long long k = skeys[i];
+            const unsigned idx = key_index(k);
+            const int x = (int)(idx % (unsigned)w), y = (int)(idx / (unsigned)w);
+            const int cx = x / cell, cy = y / cell;
+            bool blocked = false, rejected = false;
+            for (int dy = -1; dy <= 1 && !rejected; ++dy) {
+                const int yy = cy + dy;
+                if (yy < 0 || yy >= cells_y) continue;
+                for (int dx = -1; dx <= 1 && !rejected; ++dx) {
+                    const int xx = cx + dx;
+                    if (xx < 0 || xx >= cells_x) continue;
+                    const int c = yy * cells_x + xx;
+                    for (int j = cell_start[c], je = cell_start[c + 1]; j < je; ++j) {
+                        const unsigned long long kj = skeys[j];
+                        if (kj <= k) continue;  // lower priority (or itself)
+                        const unsigned jdx = key_index(kj);
+                        const long long ex = (long long)(int)(jdx % (unsigned)w) - x;
+                        const long long ey = (long long)(int)(jdx / (unsigned)w) - y;
+                        if (ex * ex + ey * ey >= d2) continue;
+                        const uint8_t sj = vs[j];
+                        if (sj == GF_KEPT) {
+                            rejected = true;
+                            break;
+                        }
+                        if (sj == GF_UNDECIDED) blocked = true;
+                    }
+                }
+            }
+            if (rejected) vs[i] = GF_REJECTED;
+            else if (!blocked) vs[i] = GF_KEPT;
+            else ++mine;
+        }
+        if (mine) atomicAdd(&und[r % 3], mine);
+        grid.sync();
+        if (*reinterpret_cast<volatile int *>(&und[r % 3]) == 0) break;
+    }
+    for (int i = tid; i < n; i += nth)
+        if (vs[i] == GF_KEPT) kept[atomicAdd(kept_count, 1)] = skeys[i];
+}
+
+// Kept candidates in priority order (keys descending), the first max_corners
+// written out.  Up to GF_SMEM_SORT keys are sorted in shared memory; more
+// (very large levels with a small min_dist) fall back to a bitonic sort in
+// global memory (keys padded to a power of two <= kept capacity).
+__global__ void __launch_bounds__(GF_SORT_THREADS) k_gftt_output(unsigned long long *kept, const int *kept_count,
+                                                                  int kept_cap, int w, int max_corners, float2 *out,
+                                                                  float *out_score, int *out_count) {
+    extern __shared__ __align__(16) unsigned long long sk[];
+    const int K = *kept_count;
     int N = 1;
-    while (N < n) N <<= 1;
-    for (int i = n + threadIdx.x; i < N; i += blockDim.x) keys[i] = 0ull;
+    while (N < K) N <<= 1;
+    const bool in_smem = N <= GF_SMEM_SORT;
+    unsigned long long *a = in_smem ? sk : kept;
+    if (in_smem)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sk[i] = i < K ? kept[i] : 0ull;
+    else
+        for (int i = K + threadIdx.x; i < N && i < kept_cap; i += blockDim.x) kept[i] = 0ull;
     __syncthreads();
     for (int k = 2; k <= N; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < N; i += blockDim.x) {
                 const int p = i ^ j;
                 if (p > i) {
-                    const unsigned long long a = keys[i], b = keys[p];
+                    const unsigned long long x = a[i], y = a[p];
                     const bool desc = (i & k) == 0;
-                    if (desc ? (a < b) : (a > b)) {
-                        keys[i] = b;
-                        keys[p] = a;
+                    if (desc ? (x < y) : (x > y)) {
+                        a[i] = y;
+                        a[p] = x;
                     }
                 }
             }
             __syncthreads();
         }
     }
-}
-
-__global__ void k_gftt_greedy(const unsigned long long *keys, const int *count, int cap, int w, int h, int min_dist,
-                              int cell, int cells_x, int cells_y, int max_corners, float2 *out, float *out_score,
-                              int *out_count) {
-    extern __shared__ __align__(16) uint8_t gf_smem[];
-    int16_t *head = reinterpret_cast<int16_t *>(gf_smem);                 // [cells_x * cells_y]
-    int16_t *next = head + ((cells_x * cells_y + 7) & ~7);                // [max_corners]
-    uint32_t *kxy = reinterpret_cast<uint32_t *>(next + ((max_corners + 7) & ~7));  // [max_corners]
-    const int lane = threadIdx.x;
-    const int ncell = cells_x * cells_y;
-    for (int i = lane; i < ncell; i += 32) head[i] = -1;
-    __syncwarp();
-    const int n = min(*count, cap);
-    const long d2 = (long)min_dist * min_dist;
-    int kept = 0;
-    for (int base = 0; base < n && kept < max_corners; base += 32) {
-        const int i = base + lane;
-        const bool have = i < n;
-        unsigned long long key = have ? keys[i] : 0ull;
-        const unsigned idx = 0xffffffffu - (unsigned)(key & 0xffffffffu);
-        const int x = have ? (int)(idx % (unsigned)w) : 0, y = have ? (int)(idx / (unsigned)w) : 0;
-        bool ok = have;
-        if (ok) {  // against the corners kept by earlier chunks
-            const int cx = x / cell, cy = y / cell;
-            for (int dy = -1; dy <= 1 && ok; ++dy) {
-                const int yy = cy + dy;
-                if (yy < 0 || yy >= cells_y) continue;
-                for (int dx = -1; dx <= 1 && ok; ++dx) {
-                    const int xx = cx + dx;
-                    if (xx < 0 || xx >= cells_x) continue;
-                    for (int e = head[yy * cells_x + xx]; e >= 0; e = next[e]) {
-                        const uint32_t p = kxy[e];
-                        const long ex = (long)(p & 0xffffu) - x, ey = (long)(p >> 16) - y;
-                        if (ex * ex + ey * ey < d2) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                }
-            }
-        }
-        // resolve the chunk in priority order
-        for (int j = 0; j < 32 && kept < max_corners; ++j) {
-            const unsigned okmask = __ballot_sync(0xffffffffu, ok);
-            if (!((okmask >> j) & 1u)) continue;
-            const int xj = __shfl_sync(0xffffffffu, x, j), yj = __shfl_sync(0xffffffffu, y, j);
-            if (lane > j && ok) {
-                const long ex = (long)x - xj, ey = (long)y - yj;
-                if (ex * ex + ey * ey < d2) ok = false;
-            }
-            if (lane == j) {
-                const int c = (y / cell) * cells_x + (x / cell);
-                kxy[kept] = (uint32_t)x | ((uint32_t)y << 16);
-                next[kept] = head[c];
-                head[c] = (int16_t)kept;
-                out[kept] = make_float2((float)x, (float)y);
-                if (out_score) out_score[kept] = __uint_as_float((unsigned)(key >> 32));
-            }
-            __syncwarp();
-            ++kept;
-        }
+    const int m = min(K, max_corners);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const unsigned long long k = a[i];
+        const unsigned idx = key_index(k);
+        out[i] = make_float2((float)(idx % (unsigned)w), (float)(idx / (unsigned)w));
+        if (out_score) out_score[i] = __uint_as_float((unsigned)(k >> 32));
     }
-    if (lane == 0) *out_count = kept;
+    if (threadIdx.x == 0) *out_count = m;
 }
 
 }  // namespace vt
@@ -200,10 +282,14 @@ using namespace vt;
 struct vt_gftt {
     int max_w, max_h;
     float *score;
-    unsigned *maxbits;  // [1], followed by the candidate count
-    int *count;
-    unsigned long long *keys;
-    int cap;
+    int *counters;  // [0] max score bits, [1] candidates, [2] kept, [3..5] undecided per round (3 slots)
+    unsigned long long *keys;   // candidates (unordered); reused for the kept keys
+    unsigned long long *skeys;  // candidates grouped by cell
+    int *rank;
+    uint8_t *state;
+    int *cell_count, *cell_start;
+    int cap, keys_cap;  // candidate capacity (pixels), keys buffer (power of two >= cap)
+    int sms, select_grid;
 };
 
 extern "C" {
@@ -217,15 +303,26 @@ vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out) {
     g->cap = max_w * max_h;
     int N = 1;
     while (N < g->cap) N <<= 1;
-    bool ok = cudaMalloc(&g->score, sizeof(float) * (size_t)max_w * max_h) == cudaSuccess &&
-              cudaMalloc(&g->maxbits, 2 * sizeof(unsigned)) == cudaSuccess &&
-              cudaMalloc(&g->keys, sizeof(unsigned long long) * (size_t)N) == cudaSuccess;
-    if (!ok) {
+    g->keys_cap = N;
+    const size_t px = (size_t)max_w * max_h;
+    bool ok = cudaMalloc(&g->score, sizeof(float) * px) == cudaSuccess &&
+              cudaMalloc(&g->counters, 8 * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&g->keys, sizeof(unsigned long long) * (size_t)N) == cudaSuccess &&
+              cudaMalloc(&g->skeys, sizeof(unsigned long long) * px) == cudaSuccess &&
+              cudaMalloc(&g->rank, sizeof(int) * px) == cudaSuccess &&
+              cudaMalloc(&g->state, px) == cudaSuccess &&
+              cudaMalloc(&g->cell_count, sizeof(int) * (px + 1)) == cudaSuccess &&
+              cudaMalloc(&g->cell_start, sizeof(int) * (px + 1)) == cudaSuccess;
+    int dev = 0, occ = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gftt_select, GF_MIS_THREADS, 0) == cudaSuccess;
+    if (!ok || occ < 1) {
         cudaGetLastError();
         vt_gftt_free(g);
-        return VT_ERR_OOM;
+        return ok ? VT_ERR_CUDA : VT_ERR_OOM;
     }
-    g->count = reinterpret_cast<int *>(g->maxbits + 1);
+    g->select_grid = g->sms * (occ < 2 ? occ : 2);  // co-resident by construction (cooperative launch)
     *out = g;
     return VT_OK;
 }
@@ -233,9 +330,14 @@ vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out) {
 void vt_gftt_free(vt_gftt *g) {
     if (!g) return;
     cudaDeviceSynchronize();
-    if (g->score) cudaFree(g->score);
-    if (g->maxbits) cudaFree(g->maxbits);
-    if (g->keys) cudaFree(g->keys);
+    cudaFree(g->score);
+    cudaFree(g->counters);
+    cudaFree(g->keys);
+    cudaFree(g->skeys);
+    cudaFree(g->rank);
+    cudaFree(g->state);
+    cudaFree(g->cell_count);
+    cudaFree(g->cell_start);
     free(g);
 }
 
@@ -250,30 +352,50 @@ vt_status vt_gftt_detect(vt_gftt *g, const vt_pyramid *p, int level, const vt_gf
         prm->border < 0 || n_mask < 0 || (n_mask > 0 && !mask_pts))
         return VT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // cells at least min_dist wide, few enough for the shared-memory heads
-    int cell = prm->min_dist;
-    while ((long)((L.w + cell - 1) / cell) * ((L.h + cell - 1) / cell) > GF_MAX_CELLS) ++cell;
-    const int cx = (L.w + cell - 1) / cell, cy = (L.h + cell - 1) / cell;
-    const size_t smem = sizeof(int16_t) * (((size_t)cx * cy + 7) & ~(size_t)7) +
-                        sizeof(int16_t) * ((prm->max_corners + 7) & ~7) + sizeof(uint32_t) * prm->max_corners;
-    if (cudaMemsetAsync(g->maxbits, 0, 2 * sizeof(unsigned), s) != cudaSuccess) {
+    const int cell = prm->min_dist;  // cells at least min_dist wide: close pairs are in neighbouring cells
+    const int cx = (L.w + cell - 1) / cell, cy = (L.h + cell - 1) / cell, ncell = cx * cy;
+    int *maxbits = g->counters, *count = g->counters + 1, *kept_count = g->counters + 2, *und = g->counters + 3;
+    if (cudaMemsetAsync(g->counters, 0, 8 * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(g->cell_count, 0, sizeof(int) * (size_t)ncell, s) != cudaSuccess) {
         cudaGetLastError();
         return VT_ERR_CUDA;
     }
-    const dim3 blk(GF_BX, GF_BY), grd((L.w + GF_BX - 1) / GF_BX, (L.h + GF_BY - 1) / GF_BY);
-    k_gftt_score<<<grd, blk, 0, s>>>(L.grad, L.gpitch, L.w, L.h, prm->block_radius, g->score, g->maxbits);
-    k_gftt_cand<<<grd, blk, 0, s>>>(g->score, L.w, L.h, g->maxbits, prm->quality, prm->nms_radius, prm->border,
-                                    reinterpret_cast<const float2 *>(mask_pts), n_mask, prm->min_dist, g->keys,
-                                    g->count, g->cap);
-    k_gftt_sort<<<1, GF_SORT_THREADS, 0, s>>>(g->keys, g->count, g->cap);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gftt_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_gftt_output, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(GF_SMEM_SORT * sizeof(unsigned long long)));
         attr = true;
     }
-    k_gftt_greedy<<<1, 32, smem, s>>>(g->keys, g->count, g->cap, L.w, L.h, prm->min_dist, cell, cx, cy,
-                                      prm->max_corners, reinterpret_cast<float2 *>(corners_out), scores_out,
-                                      count_out);
+    const dim3 blk(GF_BX, GF_BY), grd((L.w + GF_BX - 1) / GF_BX, (L.h + GF_BY - 1) / GF_BY);
+    k_gftt_score<<<grd, blk, 0, s>>>(L.grad, L.gpitch, L.w, L.h, prm->block_radius, g->score,
+                                     reinterpret_cast<unsigned *>(maxbits));
+    k_gftt_cand<<<grd, blk, 0, s>>>(g->score, L.w, L.h, reinterpret_cast<const unsigned *>(maxbits), prm->quality,
+                                    prm->nms_radius, prm->border, reinterpret_cast<const float2 *>(mask_pts), n_mask,
+                                    prm->min_dist, g->keys, count, g->cap);
+    const int gg = 4 * g->sms;
+    k_gftt_cell_count<<<gg, GF_GRID_THREADS, 0, s>>>(g->keys, count, g->cap, L.w, cell, cx, g->cell_count, g->rank);
+    k_gftt_cell_scan<<<1, GF_SCAN_THREADS, 0, s>>>(g->cell_count, ncell, g->cell_start);
+    k_gftt_cell_scatter<<<gg, GF_GRID_THREADS, 0, s>>>(g->keys, count, g->cap, L.w, cell, cx, g->cell_start, g->rank,
+                                                       g->skeys, g->state);
+    {
+        const unsigned long long *skeys = g->skeys;
+        const int *cell_start = g->cell_start;
+        uint8_t *state = g->state;
+        unsigned long long *kept = g->keys;
+        int cap = g->cap, w = L.w;
+        long long d2 = (long long)prm->min_dist * prm->min_dist;
+        void *args[] = {(void *)&skeys, (void *)&count, (void *)&cap,   (void *)&w,          (void *)&cell,
+                        (void *)&cx,    (void *)&cy,    (void *)&cell_start, (void *)&state, (void *)&und,
+                        (void *)&d2,    (void *)&kept,  (void *)&kept_count};
+        if (cudaLaunchCooperativeKernel((const void *)k_gftt_select, g->select_grid, GF_MIS_THREADS, args, 0, s) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_CUDA;
+        }
+    }
+    k_gftt_output<<<1, GF_SORT_THREADS, GF_SMEM_SORT * sizeof(unsigned long long), s>>>(
+        g->keys, kept_count, g->keys_cap, L.w, prm->max_corners, reinterpret_cast<float2 *>(corners_out), scores_out,
+        count_out);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 

@@ -77,3 +77,32 @@ def test_gftt_on_a_coarser_level():
     c = synth.make_config1(4)
     (xy, sc), (rxy, rsc) = _detect(c.I, vt.GfttParams(max_corners=200, min_dist=6, border=4), level=1, levels=3)
     assert len(xy) > 50 and np.array_equal(xy, rxy.astype(np.float32)) and np.array_equal(sc, rsc)
+
+
+def test_gftt_dense_candidates_long_chains():
+    """Every pixel of a noise image is a candidate (no suppression window),
+    min_dist 2: neighbouring candidates conflict, so the parallel selection
+    needs many rounds along chains of decreasing score."""
+    import paper_2607_01757_gb300 as vt
+
+    img = np.random.Generator(np.random.PCG64(5)).integers(0, 256, (150, 200), dtype=np.uint8)
+    prm = vt.GfttParams(max_corners=8192, quality=0.0, min_dist=2, nms_radius=0, block_radius=1, border=0)
+    (xy, sc), (rxy, rsc) = _detect(img, prm)
+    assert len(rxy) > 2000
+    assert np.array_equal(xy, rxy.astype(np.float32)) and np.array_equal(sc.view(np.uint32), rsc.view(np.uint32))
+
+
+def test_gftt_more_kept_than_the_shared_memory_sort():
+    """More than 16,384 corners survive the selection (min_dist 1), so the
+    final ordering takes the global-memory path; the first 8,192 must still
+    be the oracle's."""
+    import paper_2607_01757_gb300 as vt
+
+    img = np.random.Generator(np.random.PCG64(6)).integers(0, 256, (120, 200), dtype=np.uint8)
+    prm = vt.GfttParams(max_corners=8192, quality=0.0, min_dist=1, nms_radius=0, block_radius=1, border=0)
+    ref_pyr = oracle.build_pyramid(img, 1)
+    full, _ = oracle.gftt(ref_pyr.gx[0], ref_pyr.gy[0], 10 ** 6, 0.0, 1, 0, 1, 0)
+    assert len(full) > 16384
+    (xy, sc), (rxy, rsc) = _detect(img, prm)
+    assert len(xy) == 8192
+    assert np.array_equal(xy, rxy.astype(np.float32)) and np.array_equal(sc.view(np.uint32), rsc.view(np.uint32))
