@@ -311,6 +311,58 @@ VT_API vt_status vt_stereo_gate(const float *pts_l, const float *pts_r, const ui
                                 uint8_t *status_out, uint8_t *reason_out, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Track bookkeeping on the device: identity carry-over, thinning and
+ * spawning of new tracks for many camera streams at once (one CTA per
+ * stream; counts stay on the device, so a step needs no host round trip).
+ * The paper describes the identity rules for its matching front-end
+ * (Sec. III-C: first-frame detections all start tracks; associated features
+ * keep their identities, unassociated detections start new ones) and the
+ * LK front-end's pool (Sec. V-A: in stereo only features passing the
+ * cross-camera flow check enter it; in mono it carries itself over), with a
+ * feature cap (Sec. IV: 256).  Reading implemented (VINS-Fusion's tracker):
+ *   carry  features whose temporal track succeeded keep identity, take the
+ *          tracked position and age + 1; in order of age (descending, ties:
+ *          smaller previous index first) a survivor is kept when no kept
+ *          survivor lies at squared distance < min_dist^2 (FP32,
+ *          dx*dx + dy*dy); kept survivors rewrite the pool in that order;
+ *   spawn  accepted detections, in their (detector priority) order, fill
+ *          the pool up to `cap` with identities next_id, next_id + 1, ...
+ *          and age 1.
+ * ---------------------------------------------------------------------- */
+enum { VT_POOL_MAX = 4096 }; /* features per pool */
+
+typedef struct vt_track_pool {
+    float *pts;    /* device float2[cap] */
+    int32_t *ids;  /* device int32[cap] */
+    int32_t *ages; /* device int32[cap]: frames the feature has been tracked in */
+    int *count;    /* device int: live features (first *count entries) */
+    int *next_id;  /* device int: the stream's next unused identity */
+    int cap;       /* 1 .. VT_POOL_MAX */
+} vt_track_pool;
+
+typedef struct vt_carry_job {
+    vt_track_pool pool;     /* rewritten in place */
+    const float *tracked;   /* device float2[>= *count]: temporal result for the pool's points */
+    const uint8_t *status;  /* device uint8[>= *count]: 1 = tracked (forward-backward checked) */
+    float *mask;            /* device float2[cap], nullable: kept positions, padded with NaN to cap
+                               (a vt_gftt_detect mask with n_mask = cap) */
+} vt_carry_job;
+
+/* At most 192 jobs per call, one per pool; min_dist > 0 px.  VT_ERR_ARG for
+ * a missing array or a cap outside 1..VT_POOL_MAX. */
+VT_API vt_status vt_tracks_carry(const vt_carry_job *jobs, int njobs, float min_dist, void *cuda_stream);
+
+typedef struct vt_spawn_job {
+    vt_track_pool pool;
+    const float *corners;   /* device float2[*n_corners], in priority order */
+    const int *n_corners;   /* device int */
+    const uint8_t *accept;  /* device uint8[*n_corners], nullable (all accepted) */
+} vt_spawn_job;
+
+/* At most 192 jobs per call; the pool grows by min(accepted, cap - count). */
+VT_API vt_status vt_tracks_spawn(const vt_spawn_job *jobs, int njobs, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Batched tracking: the frames and tracking tasks of many independent camera
  * streams in one fixed sequence of persistent launches (one per pyramid
  * level, one for the last levels' gradients, one for every tracking task),

@@ -6,5 +6,6 @@ the library and fails loudly if it is missing.
 """
 
 from .vt import *  # noqa: F401,F403
-from .vt import (Pyramid, Batch, Gftt, GfttParams, GateParams, KltParams, StereoRig, VTError, LIB_PATH,  # noqa: F401
+from .vt import (Pyramid, Batch, Gftt, GfttParams, GateParams, KltParams, StereoRig, TrackPool, VTError,  # noqa: F401
+                 LIB_PATH,
                  header_functions)

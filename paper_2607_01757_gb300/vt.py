@@ -552,3 +552,60 @@ def vt_batch_set_gates(b: Batch, gates, params: GateParams) -> None:
     arr = (vt_gate_task * max(1, len(gates)))(*gates)
     prm = params.c()
     _check(_lib.vt_batch_set_gates(b, arr, len(gates), C.byref(prm)), "vt_batch_set_gates")
+
+
+# ------------------------------------------------------------------ track bookkeeping
+VT_POOL_MAX = 4096
+
+
+class vt_track_pool(C.Structure):
+    _fields_ = [("pts", vp), ("ids", vp), ("ages", vp), ("count", vp), ("next_id", vp), ("cap", i32)]
+
+
+class vt_carry_job(C.Structure):
+    _fields_ = [("pool", vt_track_pool), ("tracked", vp), ("status", vp), ("mask", vp)]
+
+
+class vt_spawn_job(C.Structure):
+    _fields_ = [("pool", vt_track_pool), ("corners", vp), ("n_corners", vp), ("accept", vp)]
+
+
+_sig("vt_tracks_carry", i32, [C.POINTER(vt_carry_job), i32, f32, vp])
+_sig("vt_tracks_spawn", i32, [C.POINTER(vt_spawn_job), i32, vp])
+
+
+class TrackPool:
+    """One stream's device-resident feature pool (positions, identities,
+    ages, live count, next identity) of capacity `cap`."""
+
+    def __init__(self, cap: int, device="cuda"):
+        import torch
+
+        self.cap = cap
+        self.pts = torch.zeros((cap, 2), dtype=torch.float32, device=device)
+        self.ids = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.ages = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.next_id = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def c(self) -> vt_track_pool:
+        return vt_track_pool(_ptr(self.pts), _ptr(self.ids), _ptr(self.ages), _ptr(self.count), _ptr(self.next_id),
+                             self.cap)
+
+
+def carry_job(pool: TrackPool, tracked, status, mask=None) -> vt_carry_job:
+    return vt_carry_job(pool.c(), _ptr(tracked), _ptr(status), _ptr(mask))
+
+
+def spawn_job(pool: TrackPool, corners, n_corners, accept=None) -> vt_spawn_job:
+    return vt_spawn_job(pool.c(), _ptr(corners), _ptr(n_corners), _ptr(accept))
+
+
+def vt_tracks_carry(jobs, min_dist: float, stream=None) -> None:
+    arr = (vt_carry_job * max(1, len(jobs)))(*jobs)
+    _check(_lib.vt_tracks_carry(arr, len(jobs), min_dist, _stream(stream)), "vt_tracks_carry")
+
+
+def vt_tracks_spawn(jobs, stream=None) -> None:
+    arr = (vt_spawn_job * max(1, len(jobs)))(*jobs)
+    _check(_lib.vt_tracks_spawn(arr, len(jobs), _stream(stream)), "vt_tracks_spawn")
