@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-gftt", action="store_true")
     ap.add_argument("--no-gate", action="store_true")
+    ap.add_argument("--no-tracks", action="store_true")
+    ap.add_argument("--no-frontend", action="store_true")
+    ap.add_argument("--fe-cap", type=int, default=256, help="feature cap per stream of the front-end loop")
     ap.add_argument("--grad", default="s16", choices=["s16", "f16", "none"],
                     help="gradient storage: int16 / half planes, or none (computed inside the tracker)")
     ap.add_argument("--served-streams", type=int, default=64)
@@ -389,6 +392,81 @@ def run_native(a, rank, world, local_rank):
                 "timing": "CUDA events from the end of the tracking launch to the end of the run, "
                           "direct launches, L2 flushed between steps"}
 
+    # ---------------- track bookkeeping (a further row, outside the headline step) -----
+    books = None
+    if not a.no_tracks:
+        pools = [vt.TrackPool(max(1, s.n_max)) for s in tr.streams]
+        corners_n = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in tr.streams]
+        masks = [torch.zeros((max(1, s.n_max), 2), device=dev) for s in tr.streams]
+        idx_cache = {}
+        carry_ms, spawn_ms, kept_n, surv_n, spawned_n = [], [], 0, 0, 0
+        for i in range(a.steps):
+            batched_step(t)  # tracking of the previous frame's keypoints (their temporal status)
+            _, _, kt_, ks_, n_t_, n_s_ = step_args(t)
+            for k, s in enumerate(tr.streams):  # pools = the previous keypoints, ages 1..5
+                n = n_t_[k]
+                if n not in idx_cache:
+                    idx_cache[n] = torch.arange(n, dtype=torch.int32, device=dev)
+                pools[k].pts[:n].copy_(kt_[k][:n])
+                pools[k].ids[:n].copy_(idx_cache[n])
+                pools[k].ages[:n].copy_(idx_cache[n] % 5 + 1)
+                pools[k].count.fill_(n)
+                pools[k].next_id.fill_(1 << 20)
+                corners_n[k].fill_(nkp[k][pingpong(t, F)])
+            cj = [vt.carry_job(pools[k], s.out_t[0], s.out_t[1], masks[k]) for k, s in enumerate(tr.streams)]
+            sj = [vt.spawn_job(pools[k], ks_[k], corners_n[k]) for k in range(len(tr.streams))]
+            flush.fill_(i & 0xFF)
+            e0, e1, e2 = ev(), None, None
+            vt.vt_tracks_carry(cj, 8.0, stream)
+            e1 = ev()
+            vt.vt_tracks_spawn(sj, stream)
+            e2 = ev()
+            torch.cuda.synchronize()
+            carry_ms.append(e0.elapsed_time(e1))
+            spawn_ms.append(e1.elapsed_time(e2))
+            for k, s in enumerate(tr.streams):
+                surv_n += int(s.out_t[1][:n_t_[k]].sum().item())
+            kept_total = sum(int(p.count.item()) for p in pools)
+            spawned_n += sum(int(p.next_id.item()) - (1 << 20) for p in pools)
+            kept_n += kept_total
+            t += 1
+        books = {"kernels": ["k_tracks_carry", "k_tracks_spawn"], "carry_ms": statistics.mean(carry_ms),
+                 "spawn_ms": statistics.mean(spawn_ms), "streams": len(tr.streams),
+                 "survivors_per_step": surv_n // a.steps, "spawned_per_step": spawned_n // a.steps,
+                 "pool_after_step": kept_n // a.steps,
+                 "params": {"min_dist_px": 8.0, "cap": "the stream's keypoint count",
+                            "detections": "the current frame's keypoints, in order"},
+                 "timing": "CUDA events around each launch (one CTA per stream), L2 flushed before"}
+
+    # ---------------- the whole front-end loop (tracking + bookkeeping + detection) -----
+    front = None
+    if not a.no_frontend:
+        from paper_2607_01757_gb300.frontend import FrontEnd
+
+        fe = FrontEnd(specs, prm, a.fe_cap, 8.0)
+        Lf = lambda t_: [left[i][pingpong(t_, F)] for i in sids]  # noqa: E731
+        Rf = lambda t_: [right[i][pingpong(t_, F)] for i in sids]  # noqa: E731
+        for t_ in range(3):
+            fe.step(Lf(t_), Rf(t_), stream)
+        torch.cuda.synchronize()
+        fms = []
+        pool_feats = 0
+        for i in range(a.steps):
+            flush.fill_(i & 0xFF)
+            e0 = ev()
+            fe.step(Lf(3 + i), Rf(3 + i), stream)
+            e1 = ev()
+            torch.cuda.synchronize()
+            fms.append(e0.elapsed_time(e1))
+            pool_feats += sum(int(fe.st[k]["pool"].count.item()) for k in range(len(specs)))
+        front = {"ms_per_step": statistics.mean(fms), "p99_ms": float(np.percentile(fms, 99)),
+                 "pool_features_per_step": pool_feats // a.steps, "cap": a.fe_cap, "min_dist_px": 8.0,
+                 "gpu_launches_per_step": fe.launches_per_step(),
+                 "steps": "temporal FB tracking of each pool, carry-over, Shi-Tomasi detection (one call per "
+                          "stream), cross-camera FB check of new corners (stereo), spawning",
+                 "timing": "CUDA events around each step, L2 flushed before"}
+        fe.free()
+
     # ---------------- plain path ----------------
     plain = None
     if not a.no_plain:
@@ -531,6 +609,8 @@ def run_native(a, rank, world, local_rank):
         "served": served,
         "gftt": gftt,
         "stereo_gate": gate,
+        "track_bookkeeping": books,
+        "frontend_loop": front,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

@@ -396,6 +396,9 @@ typedef struct vt_track_task {
     uint8_t *reason;
     int32_t *flops;
     int levels;
+    const int *n_dev; /* device int, nullable: only the first min(n, *n_dev) points are
+                         tracked (the rest of the outputs is left untouched), so a count
+                         that lives on the device (a vt_track_pool's) needs no host copy */
 } vt_track_task;
 
 typedef struct vt_batch vt_batch; /* opaque: pinned + device job tables, work counter, graphs */

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARP
         }
         const BTask &t = tasks[lo];
         const int i = p - t.p0;
+        if (t.n_dev && i >= __ldg(t.n_dev)) continue;  // beyond the device-side count
         const float2 u = t.pts_in[i];
         KParams Pt = P;
         Pt.levels = t.levels;
@@ -359,6 +360,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
         bt[t].err = tk.err;
         bt[t].reason = tk.reason;
         bt[t].flops = tk.flops;
+        bt[t].n_dev = tk.n_dev;
         bt[t].n = tk.n;
         bt[t].fb = tk.fb ? 1 : 0;
         bt[t].levels = tk.levels > 0 ? tk.levels : prm->levels;
@@ -603,6 +605,7 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
         bt[t].err = tk.err;
         bt[t].reason = tk.reason;
         bt[t].flops = tk.flops;
+        bt[t].n_dev = tk.n_dev;
         bt[t].n = tk.n;
         bt[t].fb = tk.fb ? 1 : 0;
         bt[t].levels = tk.levels > 0 ? tk.levels : prm->levels;

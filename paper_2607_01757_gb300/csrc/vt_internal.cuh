@@ -124,6 +124,7 @@ struct BTask {
     float *err;
     uint8_t *reason;
     int32_t *flops;
+    const int *n_dev;  // nullable: device-side count (points beyond it are skipped)
     int n, fb, p0, levels;
 };
 

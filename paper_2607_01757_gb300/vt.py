@@ -300,7 +300,7 @@ class vt_frame_job(C.Structure):
 
 class vt_track_task(C.Structure):
     _fields_ = [("prev", vp), ("cur", vp), ("pts_in", vp), ("n", i32), ("fb", i32), ("pts_out", vp),
-                ("status", vp), ("err", vp), ("reason", vp), ("flops", vp), ("levels", i32)]
+                ("status", vp), ("err", vp), ("reason", vp), ("flops", vp), ("levels", i32), ("n_dev", vp)]
 
 
 _sig("vt_batch_create", i32, [i32, i32, C.POINTER(vp)])
@@ -371,9 +371,11 @@ def frame_job(img, pyr: Pyramid) -> vt_frame_job:
 
 
 def track_task(prev: Pyramid, cur: Pyramid, pts_in, pts_out, status, err=None, fb=True, reason=None,
-               flops=None, levels=0) -> vt_track_task:
+               flops=None, levels=0, n_dev=None) -> vt_track_task:
+    """n_dev: optional device int; only the first min(n, *n_dev) points are tracked."""
     return vt_track_task(prev.handle, cur.handle, _ptr(pts_in), int(pts_in.shape[0]), int(bool(fb)),
-                         _ptr(pts_out), _ptr(status), _ptr(err), _ptr(reason), _ptr(flops), int(levels))
+                         _ptr(pts_out), _ptr(status), _ptr(err), _ptr(reason), _ptr(flops), int(levels),
+                         _ptr(n_dev))
 
 
 def vt_batch_set(b: Batch, frames, tasks, params: KltParams, grad_type: int = VT_GRAD_S16) -> None:

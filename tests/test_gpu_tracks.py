@@ -152,3 +152,36 @@ def test_bookkeeping_loop_matches_oracle():
         vt.vt_tracks_spawn(sjobs)
         for k, cap in enumerate(caps):
             _check(pools[k], refs[k], f"step {step} stream {k}")
+
+
+def test_track_task_device_count():
+    """A tracking task with a device-side count tracks exactly its first
+    *n_dev points (bit-identical to a task of that size) and leaves the rest
+    of its outputs untouched."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    import synth
+
+    c = synth.make_config1(1)
+    prm = vt.KltParams(win=21, levels=4)
+    pI = vt.vt_pyramid_build_grad(c.I, 4, vt.VT_GRAD_S16)
+    pJ = vt.vt_pyramid_build_grad(c.J, 4, vt.VT_GRAD_S16)
+    pts = torch.from_numpy(np.ascontiguousarray(c.pts, np.float32)).cuda()
+    n, k = pts.shape[0], 97
+    outs = []
+    for n_dev in (torch.tensor([k], dtype=torch.int32, device="cuda"), None):
+        o = torch.full((n, 2), -5.0, device="cuda")
+        st = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
+        b = vt.Batch(2, 1)
+        src = pts if n_dev is not None else pts[:k]
+        vt.vt_batch_set(b, [], [vt.track_task(pI, pJ, src, o, st, fb=True, n_dev=n_dev)], prm)
+        vt.vt_batch_run(b)
+        torch.cuda.synchronize()
+        outs.append((o.cpu().numpy(), st.cpu().numpy()))
+        b.free()
+    (o1, s1), (o2, s2) = outs
+    assert np.array_equal(o1[:k].view(np.uint32), o2[:k].view(np.uint32)) and np.array_equal(s1[:k], s2[:k])
+    assert (o1[k:] == -5.0).all() and (s1[k:] == 7).all()
+    pI.free()
+    pJ.free()
