@@ -239,18 +239,23 @@ VT_API vt_status vt_klt_track_fb(const vt_pyramid *prev, const vt_pyramid *cur, 
  * that order; *count_out (a device int) receives how many.
  * ---------------------------------------------------------------------- */
 typedef struct vt_gftt_params {
-    int max_corners;  /* 0 .. 8192 */
+    int max_corners;  /* 0 .. 8192 (vt_gftt_detect; per job in vt_gftt_detect_many) */
     float quality;    /* relative threshold, e.g. 0.01 */
     int min_dist;     /* >= 1 px */
-    int nms_radius;   /* >= 0 */
+    int nms_radius;   /* 0 .. 8 */
     int block_radius; /* 0 .. 3 (1 = 3x3 block) */
     int border;       /* >= 0 px */
 } vt_gftt_params;
 
 typedef struct vt_gftt vt_gftt; /* opaque: workspace for levels up to max_w x max_h */
 
-/* Allocates the workspace (score map, candidate keys). */
+/* Allocates the workspace (score map, candidate keys) for one level of at
+ * most max_w x max_h pixels. */
 VT_API vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out);
+
+/* Workspace for vt_gftt_detect_many: the levels of one call may hold up to
+ * max_pixels pixels together (about 50 bytes of device memory per pixel). */
+VT_API vt_status vt_gftt_create_pixels(long long max_pixels, vt_gftt **out);
 
 /* Detect corners on level `level` of `p`.  mask_pts: device float2[n_mask]
  * (nullable when n_mask == 0).  corners_out: device float2[max_corners];
@@ -259,6 +264,24 @@ VT_API vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out);
 VT_API vt_status vt_gftt_detect(vt_gftt *g, const vt_pyramid *p, int level, const vt_gftt_params *prm,
                                 const float *mask_pts, int n_mask, float *corners_out, float *scores_out,
                                 int *count_out, void *cuda_stream);
+
+/* Many frames in one sequence of launches (every kernel covers every
+ * frame): one job per level, each with its own mask and outputs, the
+ * detector parameters of `prm` (its max_corners is ignored: per job).
+ * At most 64 jobs; VT_ERR_ARG when the levels' pixels exceed the workspace. */
+typedef struct vt_gftt_job {
+    const vt_pyramid *pyr; /* VT_GRAD_S16 gradients */
+    int level;
+    const float *mask_pts; /* device float2[n_mask], nullable when n_mask == 0 */
+    int n_mask;
+    float *corners_out; /* device float2[max_corners] */
+    float *scores_out;  /* device float[max_corners], nullable */
+    int *count_out;     /* device int */
+    int max_corners;    /* 0 .. 8192 */
+} vt_gftt_job;
+
+VT_API vt_status vt_gftt_detect_many(vt_gftt *g, const vt_gftt_job *jobs, int njobs, const vt_gftt_params *prm,
+                                     void *cuda_stream);
 
 /* Frees the workspace (synchronises the device first; NULL is ignored). */
 VT_API void vt_gftt_free(vt_gftt *g);

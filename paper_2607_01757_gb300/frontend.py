@@ -19,8 +19,8 @@ round trip:
   5. spawn new tracks from the accepted corners until the pool is full (one
      launch for every stream).
 
-Step 3 runs one detector call per stream; everything else is one launch (or
-one batched run) for all streams.
+Every step is one launch (or one batched run, or one detector call) for all
+streams.
 """
 
 from __future__ import annotations
@@ -53,10 +53,12 @@ class FrontEnd:
                 "pool": vt.TrackPool(cap, device),
                 "tracked": z(cap, 2), "status": z(cap, dt=torch.uint8),
                 "mask": torch.full((cap, 2), float("nan"), device=device),
-                "gftt": vt.Gftt(sp.w, sp.h), "corners": z(cap, 2), "ncorners": z(1, dt=torch.int32),
+                "corners": z(cap, 2), "ncorners": z(1, dt=torch.int32),
                 "right": z(cap, 2) if sp.stereo else None, "right_st": z(cap, dt=torch.uint8) if sp.stereo else None,
             }
             self.st.append(d)
+        self.gftt = vt.vt_gftt_create_pixels(sum(sp.w * sp.h for sp in self.specs[:64]) if len(self.specs) <= 64
+                                             else 64 * max(sp.w * sp.h for sp in self.specs))
         nf = sum(2 if sp.stereo else 1 for sp in self.specs)
         self.batch_a = vt.Batch(max(1, nf), max(1, len(self.specs)))
         self.batch_b = vt.Batch(1, max(1, len(self.specs)))
@@ -87,10 +89,10 @@ class FrontEnd:
             vt.vt_tracks_carry([vt.carry_job(self.st[k]["pool"], self.st[k]["tracked"], self.st[k]["status"],
                                              self.st[k]["mask"]) for k in range(len(self.specs))], self.min_dist,
                                stream)
-        for k in range(len(self.specs)):
-            d = self.st[k]
-            vt.vt_gftt_detect(d["gftt"], self._cur(k), 0, self.detect, d["corners"], d["ncorners"], mask=d["mask"],
-                              stream=stream)
+        jobs = [vt.gftt_job(self._cur(k), 0, d["corners"], d["ncorners"], self.cap, mask=d["mask"])
+                for k, d in enumerate(self.st)]
+        for c0 in range(0, len(jobs), 64):  # at most 64 frames per detector call
+            vt.vt_gftt_detect_many(self.gftt, jobs[c0:c0 + 64], self.detect, stream)
         stereo_tasks = []
         for k, sp in enumerate(self.specs):
             if sp.stereo:
@@ -120,7 +122,7 @@ class FrontEnd:
         reported by vt_batch_info; 7 per detector call)."""
         a = vt.vt_batch_info(self.batch_a)["launches_per_run"]
         b = vt.vt_batch_info(self.batch_b)["launches_per_run"] if any(sp.stereo for sp in self.specs) else 0
-        return a + 1 + 7 * len(self.specs) + b + 1
+        return a + 1 + 7 * ((len(self.specs) + 63) // 64) + b + 1
 
     def pool(self, k):
         """(positions, identities, ages) of stream k's pool, on the host."""
@@ -136,4 +138,4 @@ class FrontEnd:
                 p.free()
             if d["pyr_r"] is not None:
                 d["pyr_r"].free()
-            d["gftt"].free()
+        self.gftt.free()

@@ -469,6 +469,35 @@ def vt_gftt_create(max_w: int, max_h: int) -> Gftt:
     return Gftt(max_w, max_h)
 
 
+class vt_gftt_job(C.Structure):
+    _fields_ = [("pyr", vp), ("level", i32), ("mask_pts", vp), ("n_mask", i32), ("corners_out", vp),
+                ("scores_out", vp), ("count_out", vp), ("max_corners", i32)]
+
+
+_sig("vt_gftt_create_pixels", i32, [C.c_longlong, C.POINTER(vp)])
+_sig("vt_gftt_detect_many", i32, [vp, C.POINTER(vt_gftt_job), i32, C.POINTER(vt_gftt_params), vp])
+
+
+def vt_gftt_create_pixels(max_pixels: int) -> Gftt:
+    g = Gftt.__new__(Gftt)
+    hd = vp()
+    _check(_lib.vt_gftt_create_pixels(int(max_pixels), C.byref(hd)), "vt_gftt_create_pixels")
+    g.handle = hd.value
+    return g
+
+
+def gftt_job(pyr: Pyramid, level: int, corners_out, count_out, max_corners: int, scores_out=None,
+             mask=None) -> vt_gftt_job:
+    return vt_gftt_job(pyr.handle, level, _ptr(mask), 0 if mask is None else int(mask.shape[0]), _ptr(corners_out),
+                       _ptr(scores_out), _ptr(count_out), int(max_corners))
+
+
+def vt_gftt_detect_many(g: Gftt, jobs, params: GfttParams, stream=None) -> None:
+    arr = (vt_gftt_job * max(1, len(jobs)))(*jobs)
+    prm = params.c()
+    _check(_lib.vt_gftt_detect_many(g, arr, len(jobs), C.byref(prm), _stream(stream)), "vt_gftt_detect_many")
+
+
 def vt_gftt_free(g: Gftt) -> None:
     g.free()
 

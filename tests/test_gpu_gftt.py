@@ -41,6 +41,8 @@ CASES = [
     dict(max_corners=8192, quality=0.0, min_dist=1, nms_radius=0, block_radius=0, border=0),
     dict(max_corners=300, quality=0.05, min_dist=30, nms_radius=4, block_radius=2, border=20),
     dict(max_corners=0, quality=0.01, min_dist=10, nms_radius=4, block_radius=1, border=10),
+    # wide spacing: the top candidates alone cannot yield max_corners, so the selection runs again over all
+    dict(max_corners=150, quality=0.001, min_dist=45, nms_radius=2, block_radius=1, border=3),
 ]
 
 
@@ -105,4 +107,61 @@ def test_gftt_more_kept_than_the_shared_memory_sort():
     assert len(full) > 16384
     (xy, sc), (rxy, rsc) = _detect(img, prm)
     assert len(xy) == 8192
+    assert np.array_equal(xy, rxy.astype(np.float32)) and np.array_equal(sc.view(np.uint32), rsc.view(np.uint32))
+
+
+def test_gftt_many_frames_in_one_call():
+    """Frames of different shapes, masks and caps in one call equal the
+    oracle frame by frame (and hence the single-frame call)."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    rng = np.random.Generator(np.random.PCG64(8))
+    shapes = [(480, 640), (120, 200), (600, 960), (33, 47), (480, 752)]
+    imgs = [synth.make_config1(1).I[:h, :w] if h <= 480 and w <= 752 else
+            rng.integers(0, 256, (h, w), dtype=np.uint8) for h, w in shapes]
+    prm = vt.GfttParams(max_corners=0, quality=0.01, min_dist=7, nms_radius=3, block_radius=1, border=6)
+    caps = [300, 8192, 1500, 5, 0]
+    pyrs = [vt.vt_pyramid_build_grad(np.ascontiguousarray(im), 1, vt.VT_GRAD_S16) for im in imgs]
+    g = vt.vt_gftt_create_pixels(sum(h * w for h, w in shapes))
+    outs, jobs, masks = [], [], []
+    for k, (p, cap) in enumerate(zip(pyrs, caps)):
+        o = torch.zeros((max(1, cap), 2), device="cuda")
+        sc = torch.zeros(max(1, cap), device="cuda")
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        mask = None
+        if k == 0:
+            mask = torch.from_numpy(rng.uniform(0, 600, (40, 2)).astype(np.float32)).cuda()
+        masks.append(mask)
+        outs.append((o, sc, n))
+        jobs.append(vt.gftt_job(p, 0, o, n, cap, scores_out=sc, mask=mask))
+    vt.vt_gftt_detect_many(g, jobs, prm)
+    torch.cuda.synchronize()
+    for k, (im, cap) in enumerate(zip(imgs, caps)):
+        rp = oracle.build_pyramid(np.ascontiguousarray(im), 1)
+        m = None if masks[k] is None else masks[k].cpu().numpy().astype(np.float64)
+        rxy, rsc = oracle.gftt(rp.gx[0], rp.gy[0], cap, prm.quality, prm.min_dist, prm.nms_radius, prm.block_radius,
+                               prm.border, m)
+        o, sc, n = outs[k]
+        cnt = int(n.item())
+        assert cnt == len(rxy), (k, cnt, len(rxy))
+        assert np.array_equal(o[:cnt].cpu().numpy(), rxy.astype(np.float32))
+        assert np.array_equal(sc[:cnt].cpu().numpy().view(np.uint32), rsc.view(np.uint32))
+    g.free()
+    for p in pyrs:
+        p.free()
+
+
+def test_gftt_top_set_larger_than_shared_memory():
+    """Many kept corners with few distinct scores (a periodic pattern): the
+    top histogram bins hold more keys than the shared-memory sort, so the
+    whole kept set is sorted in global memory; still the oracle's list."""
+    import paper_2607_01757_gb300 as vt
+
+    yy, xx = np.mgrid[0:160, 0:240]
+    img = (((xx // 2) + (yy // 2)) % 2 * 200 + 20).astype(np.uint8)
+    prm = vt.GfttParams(max_corners=8192, quality=0.0, min_dist=1, nms_radius=0, block_radius=1, border=0)
+    (xy, sc), (rxy, rsc) = _detect(img, prm)
+    assert len(rxy) == 8192
     assert np.array_equal(xy, rxy.astype(np.float32)) and np.array_equal(sc.view(np.uint32), rsc.view(np.uint32))
