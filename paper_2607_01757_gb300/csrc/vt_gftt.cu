@@ -4,35 +4,35 @@
 // stored int16 Scharr gradients.  Every launch covers every frame ("job") of
 // the call:
 //
-//   K6a k_gftt_score   a, b, c = (2br+1)^2 box sums of gx^2, gx gy, gy^2 (exact
-//                      integers, from a shared-memory tile of gradient words
-//                      with reflect-101 borders), lambda_min in FP32 with
-//                      explicit round-to-nearest operations, clamped at 0; one
-//                      atomic maximum per frame.
-//   K6b k_gftt_cand    lambda >= quality * max, lambda > 0, outside the border,
-//                      the maximum of its (2nms+1)^2 window (ties to the
-//                      smaller index; a shared-memory tile of scores), far
-//                      enough from every mask point (a byte map the mask
-//                      kernel rasterises with the same FP32 test): a 64-bit
-//                      key (score bits, ~pixel) in the frame's candidate
-//                      segment.
-//   K6c cell grid      counting sort of each frame's candidates into cells at
-//                      least min_dist wide (count, per-frame scan, scatter).
-//   K6d k_gftt_select  the greedy min-distance selection in priority order,
-//                      resolved in parallel rounds over the cell grids
-//                      (cooperative launch, grid-wide barrier per round),
-//                      first over the top candidates only (a score-histogram
-//                      threshold leaving a few times max_corners of them: the
-//                      greedy's decisions depend only on higher-priority
-//                      candidates, so its first max_corners kept are the
-//                      same), again over all candidates when that was not
-//                      enough.
-//   K6e k_gftt_output  per frame (one CTA): the first max_corners kept
-//                      candidates in priority order -- a histogram of the
-//                      score bits picks the smallest top set that holds them,
-//                      which is sorted in shared memory (a bitonic sort of
-//                      the whole kept set in global memory when that set is
-//                      too large).
+//   K6a k_gftt_local   per tile: the gradient words (reflect-101 borders) in
+//                      shared memory; a, b, c = (2br+1)^2 box sums of gx^2,
+//                      gx gy, gy^2 (exact integers) and lambda_min in FP32 with
+//                      explicit round-to-nearest operations, clamped at 0, for
+//                      the tile and an nms halo; the frame maximum (one atomic
+//                      per tile); every pixel outside the border that is the
+//                      maximum of its (2nms+1)^2 window (separable maximum;
+//                      ties to the smaller index) and not within min_dist of a
+//                      mask point (a byte map the mask kernel rasterises with
+//                      the same FP32 test) is a local maximum: a 64-bit key
+//                      (score bits, ~pixel).
+//   K6b k_gftt_filter  local maxima with lambda >= quality * max: the frame's
+//                      candidates.
+//   K6c first pass     per frame (one CTA, k_gftt_greedy_top): the candidates
+//                      of the smallest set of top score-histogram bins holding
+//                      a few times max_corners of them, sorted in shared
+//                      memory, then a warp's greedy min-distance pass in
+//                      priority order -- the greedy's decisions depend only on
+//                      higher-priority candidates, so its first max_corners
+//                      kept are the full greedy's.
+//   K6d second pass    frames the first pass could not settle (fewer kept than
+//                      max_corners while more candidates exist, or too many
+//                      participants): a counting sort of all candidates into
+//                      cells at least min_dist wide, the greedy resolved in
+//                      parallel rounds over the cells (k_gftt_select:
+//                      cooperative launch, a grid-wide barrier per round), and
+//                      k_gftt_output ordering the kept (a score-histogram top
+//                      set sorted in shared memory, or a bitonic sort of all
+//                      kept in global memory).
 // Every decision is taken on the same FP32 values the oracle computes, so the
 // corner lists are exact.
 #include <cooperative_groups.h>
@@ -46,7 +46,7 @@ namespace cg = cooperative_groups;
 
 namespace vt {
 
-constexpr int GF_TX = 32, GF_TY = 8;  // score / candidate tiles
+constexpr int GF_TX = 64, GF_TY = 16;  // score / local-maximum tiles
 constexpr int GF_MAX_BR = 3, GF_MAX_NMS = 8;
 constexpr int GF_OUT_THREADS = 1024;
 constexpr int GF_SCAN_THREADS = 1024;
@@ -100,15 +100,17 @@ struct GJobs {
 // Per-frame counters in the workspace.
 struct GCount {
     unsigned maxbits;  // maximum score bits
+    int lmax;          // local maxima (before the quality threshold)
     int cand;          // candidates
     int part;          // candidates taking part in the selection (keys >= lo)
     int kept;          // kept by the selection
     int retry;         // the top set was too small: select again over every candidate
-    int pad;
     unsigned long long lo;
 };
 
-__device__ __forceinline__ float gftt_score(long long a, long long b, long long c) {
+// a, b, c fit in 32 bits (at most 49 * 4080^2), so their conversions to float
+// round exactly like the oracle's 64-bit ones.
+__device__ __forceinline__ float gftt_score(int a, int b, int c) {
     const float fa = (float)a, fb = (float)b, fc = (float)c;
     const float d = __fsub_rn(fa, fc);
     const float q = __fadd_rn(__fmul_rn(d, d), __fmul_rn(4.0f, __fmul_rn(fb, fb)));
@@ -128,50 +130,6 @@ __device__ __forceinline__ int tile_job(const GJobs &J, int t) {
 }
 
 __device__ __forceinline__ unsigned key_pixel(unsigned long long k) { return 0xffffffffu - (unsigned)(k & 0xffffffffu); }
-
-__global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_score(const __grid_constant__ GJobs J, float *score,
-                                                             GCount *cnt) {
-    constexpr int SW = GF_TX + 2 * GF_MAX_BR, SH = GF_TY + 2 * GF_MAX_BR;
-    __shared__ uint32_t s[SH][SW];
-    __shared__ unsigned wm[GF_TX * GF_TY / 32];
-    const int jb = tile_job(J, blockIdx.x);
-    const GJob &G = J.j[jb];
-    const int t = blockIdx.x - G.tile0, ty = t / G.tiles_x, tx = t - ty * G.tiles_x;
-    const int x0 = tx * GF_TX, y0 = ty * GF_TY, br = J.br;
-    const int tid = threadIdx.y * GF_TX + threadIdx.x;
-    for (int i = tid; i < (GF_TY + 2 * br) * (GF_TX + 2 * br); i += GF_TX * GF_TY) {
-        const int r = i / (GF_TX + 2 * br), c = i - r * (GF_TX + 2 * br);
-        const int yy = refl101(y0 + r - br, G.h), xx = refl101(x0 + c - br, G.w);
-        s[r][c] = __ldg(G.grad + (size_t)yy * G.gpitch + xx);
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    float sc = 0.0f;
-    if (x < G.w && y < G.h) {
-        int a = 0, b = 0, c = 0;  // at most 49 * 4080^2 < 2^31
-        for (int j = 0; j <= 2 * br; ++j)
-            for (int i = 0; i <= 2 * br; ++i) {
-                const uint32_t v = s[threadIdx.y + j][threadIdx.x + i];
-                const int u = (int16_t)(v & 0xffffu), w = (int16_t)(v >> 16);
-                a += u * u;
-                b += u * w;
-                c += w * w;
-            }
-        sc = gftt_score(a, b, c);
-        score[(size_t)G.px0 + (size_t)y * G.w + x] = sc;
-    }
-    // frame maximum (scores are >= 0, so their bit patterns order like the values)
-    unsigned m = __float_as_uint(sc);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((tid & 31) == 0) wm[tid >> 5] = m;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned mm = 0;
-        for (int k = 0; k < GF_TX * GF_TY / 32; ++k) mm = max(mm, wm[k]);
-        atomicMax(&cnt[jb].maxbits, mm);
-    }
-}
 
 // Pixels within min_dist of a mask point, marked in a byte map (one warp per
 // mask point, blockIdx.y: frame).  The test is the candidate test itself,
@@ -199,39 +157,79 @@ __global__ void k_gftt_mask(const __grid_constant__ GJobs J, uint8_t *masked) {
     }
 }
 
-__global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_cand(const __grid_constant__ GJobs J, const float *score,
-                                                            GCount *cnt, const uint8_t *masked,
-                                                            unsigned long long *keys) {
-    constexpr int SW = GF_TX + 2 * GF_MAX_NMS, SH = GF_TY + 2 * GF_MAX_NMS;
-    __shared__ float s[SH][SW];
-    __shared__ float rmax[SH][GF_TX];  // row maxima over each output column's window
+// Scores, frame maximum and local maxima in one pass over the gradients
+// (one CTA per GF_TX x GF_TY tile of one frame): the gradient words of the
+// tile plus an (nms + br) halo (reflect-101) are staged in shared memory, the
+// scores of the tile plus an nms halo computed from them (outside the image:
+// -1, which never competes), and each output pixel outside the border that
+// is the maximum of its window (separable maximum; an equal score at a
+// smaller index wins the tie) and not masked goes to the frame's list of
+// local maxima.  The quality threshold, which needs the frame maximum, is
+// applied afterwards (k_gftt_filter).
+__global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_local(const __grid_constant__ GJobs J, GCount *cnt,
+                                                             const uint8_t *masked, unsigned long long *lmax) {
+    constexpr int HG = GF_MAX_NMS + GF_MAX_BR;
+    __shared__ uint32_t sg[GF_TY + 2 * HG][GF_TX + 2 * HG];
+    __shared__ float sc[GF_TY + 2 * GF_MAX_NMS][GF_TX + 2 * GF_MAX_NMS];
+    __shared__ float rmax[GF_TY + 2 * GF_MAX_NMS][GF_TX];
+    __shared__ unsigned wm[GF_TX * GF_TY / 32];
     const int jb = tile_job(J, blockIdx.x);
     const GJob &G = J.j[jb];
     const int t = blockIdx.x - G.tile0, ty = t / G.tiles_x, tx = t - ty * G.tiles_x;
-    const int x0 = tx * GF_TX, y0 = ty * GF_TY, nms = J.nms;
+    const int x0 = tx * GF_TX, y0 = ty * GF_TY, nms = J.nms, br = J.br, hg = nms + br;
     const int tid = threadIdx.y * GF_TX + threadIdx.x;
-    const float *sp = score + G.px0;
-    for (int i = tid; i < (GF_TY + 2 * nms) * (GF_TX + 2 * nms); i += GF_TX * GF_TY) {
-        const int r = i / (GF_TX + 2 * nms), c = i - r * (GF_TX + 2 * nms);
-        const int yy = y0 + r - nms, xx = x0 + c - nms;
-        // outside the image nothing competes (scores are >= 0)
-        s[r][c] = (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) ? sp[(size_t)yy * G.w + xx] : -1.0f;
+    const int gw = GF_TX + 2 * hg, gh = GF_TY + 2 * hg;
+    const bool interior = x0 - hg >= 0 && y0 - hg >= 0 && x0 + GF_TX + hg <= G.w && y0 + GF_TY + hg <= G.h;
+    for (int r = threadIdx.y; r < gh; r += GF_TY) {
+        const int yy = interior ? y0 + r - hg : refl101(y0 + r - hg, G.h);
+        const uint32_t *row = G.grad + (size_t)yy * G.gpitch;
+        for (int c = threadIdx.x; c < gw; c += GF_TX)
+            sg[r][c] = __ldg(row + (interior ? x0 + c - hg : refl101(x0 + c - hg, G.w)));
     }
     __syncthreads();
-    // separable window maximum: rows first, then the column of row maxima
-    for (int i = tid; i < (GF_TY + 2 * nms) * GF_TX; i += GF_TX * GF_TY) {
-        const int r = i / GF_TX, c = i - r * GF_TX;
-        float m = s[r][c];
-        for (int k = 1; k <= 2 * nms; ++k) m = fmaxf(m, s[r][c + k]);
+    const int sw = GF_TX + 2 * nms, sh = GF_TY + 2 * nms;
+    for (int r = threadIdx.y; r < sh; r += GF_TY)
+        for (int c = threadIdx.x; c < sw; c += GF_TX) {
+        const int yy = y0 + r - nms, xx = x0 + c - nms;
+        float v = -1.0f;
+        if (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) {
+            int a = 0, b = 0, cc = 0;  // at most 49 * 4080^2 < 2^31
+            for (int j = 0; j <= 2 * br; ++j)
+                for (int k = 0; k <= 2 * br; ++k) {
+                    const uint32_t g = sg[r + j][c + k];
+                    const int u = (int16_t)(g & 0xffffu), w = (int16_t)(g >> 16);
+                    a += u * u;
+                    b += u * w;
+                    cc += w * w;
+                }
+            v = gftt_score(a, b, cc);
+        }
+        sc[r][c] = v;
+        }
+    __syncthreads();
+    for (int r = threadIdx.y; r < sh; r += GF_TY) {  // row maxima over each output column's window
+        const int c = threadIdx.x;
+        float m = sc[r][c];
+        for (int k = 1; k <= 2 * nms; ++k) m = fmaxf(m, sc[r][c + k]);
         rmax[r][c] = m;
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool inside = x < G.w && y < G.h;
+    const float v = inside ? sc[threadIdx.y + nms][threadIdx.x + nms] : 0.0f;
+    // frame maximum (scores are >= 0, so their bit patterns order like the values)
+    unsigned m = __float_as_uint(v);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) wm[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned mm = 0;
+        for (int k = 0; k < GF_TX * GF_TY / 32; ++k) mm = max(mm, wm[k]);
+        atomicMax(&cnt[jb].maxbits, mm);
+    }
     const int border = J.border;
-    if (x < border || y < border || x >= G.w - border || y >= G.h - border) return;
-    const float v = s[threadIdx.y + nms][threadIdx.x + nms];
-    const float thr = __fmul_rn(J.quality, __uint_as_float(cnt[jb].maxbits));
-    if (!(v >= thr) || !(v > 0.0f)) return;
+    if (!inside || !(v > 0.0f) || x < border || y < border || x >= G.w - border || y >= G.h - border) return;
     float wmax = rmax[threadIdx.y][threadIdx.x];
     for (int k = 1; k <= 2 * nms; ++k) wmax = fmaxf(wmax, rmax[threadIdx.y + k][threadIdx.x]);
     if (wmax > v) return;  // a strictly larger score in the window
@@ -239,13 +237,26 @@ __global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_cand(const __grid_constan
     for (int j = -nms; j <= 0; ++j)
         for (int i = -nms; i <= nms; ++i) {
             if (j == 0 && i >= 0) break;
-            // a tie goes to the smaller row-major index: (j, i) before (0, 0)
-            if (s[threadIdx.y + nms + j][threadIdx.x + nms + i] == v) return;
+            if (sc[threadIdx.y + nms + j][threadIdx.x + nms + i] == v) return;  // (j, i) comes first
         }
     if (G.n_mask > 0 && masked[(size_t)G.px0 + (size_t)y * G.w + x]) return;
     const unsigned gpx = (unsigned)G.px0 + (unsigned)(y * G.w + x);
-    const int slot = atomicAdd(&cnt[jb].cand, 1);
-    keys[(size_t)G.px0 + slot] = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - gpx);
+    const int slot = atomicAdd(&cnt[jb].lmax, 1);
+    lmax[(size_t)G.px0 + slot] = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - gpx);
+}
+
+// Local maxima at or above quality * (frame maximum) become the frame's
+// candidates (blockIdx.y: frame).
+__global__ void k_gftt_filter(const __grid_constant__ GJobs J, GCount *cnt, const unsigned long long *lmax,
+                              unsigned long long *keys) {
+    const GJob &G = J.j[blockIdx.y];
+    GCount &C = cnt[blockIdx.y];
+    const int n = C.lmax;
+    const float thr = __fmul_rn(J.quality, __uint_as_float(C.maxbits));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = lmax[(size_t)G.px0 + i];
+        if (__uint_as_float((unsigned)(k >> 32)) >= thr) keys[(size_t)G.px0 + atomicAdd(&C.cand, 1)] = k;
+    }
 }
 
 // Candidates into cells at least min_dist wide, so every pair closer than
@@ -692,7 +703,6 @@ using namespace vt;
 
 struct vt_gftt {
     long long cap;  // pixels of all frames of one call
-    float *score;
     GCount *cnt;  // [kMaxGfttJobs]
     int *und;     // [3] undecided candidates per round
     unsigned long long *keys, *skeys, *kept;
@@ -718,8 +728,7 @@ vt_status vt_gftt_create_pixels(long long max_pixels, vt_gftt **out) {
     g->max_w = g->max_h = 65535;
     const size_t px = (size_t)max_pixels;
     // cells: at most one per pixel plus one end entry per frame
-    bool ok = cudaMalloc(&g->score, sizeof(float) * px) == cudaSuccess &&
-              cudaMalloc(&g->cnt, sizeof(GCount) * kMaxGfttJobs) == cudaSuccess &&
+    bool ok = cudaMalloc(&g->cnt, sizeof(GCount) * kMaxGfttJobs) == cudaSuccess &&
               cudaMalloc(&g->und, 4 * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&g->keys, sizeof(unsigned long long) * px) == cudaSuccess &&
               cudaMalloc(&g->skeys, sizeof(unsigned long long) * px) == cudaSuccess &&
@@ -755,7 +764,6 @@ vt_status vt_gftt_create(int max_w, int max_h, vt_gftt **out) {
 void vt_gftt_free(vt_gftt *g) {
     if (!g) return;
     cudaDeviceSynchronize();
-    cudaFree(g->score);
     cudaFree(g->cnt);
     cudaFree(g->und);
     cudaFree(g->keys);
@@ -841,7 +849,6 @@ vt_status vt_gftt_detect_many(vt_gftt *g, const vt_gftt_job *jobs, int njobs, co
         attr = true;
     }
     const dim3 blk(GF_TX, GF_TY);
-    k_gftt_score<<<tiles, blk, 0, s>>>(J, g->score, g->cnt);
     int max_mask = 0;
     for (int i = 0; i < njobs; ++i) max_mask = max(max_mask, jobs[i].n_mask);
     if (max_mask > 0) {  // the state bytes serve as the mask map until the cell scatter rewrites them
@@ -852,8 +859,9 @@ vt_status vt_gftt_detect_many(vt_gftt *g, const vt_gftt_job *jobs, int njobs, co
         const dim3 mgrid((unsigned)min(1024, (max_mask + 7) / 8), (unsigned)njobs);
         k_gftt_mask<<<mgrid, 256, 0, s>>>(J, g->state);
     }
-    k_gftt_cand<<<tiles, blk, 0, s>>>(J, g->score, g->cnt, g->state, g->keys);
+    k_gftt_local<<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys);
     const dim3 cgrid((unsigned)((4 * g->sms + njobs - 1) / njobs), (unsigned)njobs);
+    k_gftt_filter<<<cgrid, GF_GRID_THREADS, 0, s>>>(J, g->cnt, g->skeys, g->keys);
     k_gftt_hist<<<cgrid, GF_GRID_THREADS, 0, s>>>(J, g->cnt, g->keys, g->hist);
     k_gftt_top<<<njobs, GF_HIST / 4, 0, s>>>(J, g->cnt, g->hist);
     k_gftt_greedy_top<<<njobs, GF_GR_THREADS, sizeof(GreedySmem), s>>>(J, g->cnt, g->keys);
