@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-gate", action="store_true")
     ap.add_argument("--no-tracks", action="store_true")
     ap.add_argument("--no-frontend", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only", choices=["gftt"], default=None,
+                    help="run one section alone (profiler captures); prints that section only")
     ap.add_argument("--fe-cap", type=int, default=256, help="feature cap per stream of the front-end loop")
     ap.add_argument("--grad", default="s16", choices=["s16", "f16", "none"],
                     help="gradient storage: int16 / half planes, or none (computed inside the tracker)")
@@ -273,6 +276,27 @@ def run_native(a, rank, world, local_rank):
     t = 0
     batched_step(t)  # frame 0: pyramids only (no previous frame yet)
     t += 1
+    tune = None
+    if not a.no_autotune:  # launch shape of the tracking launch, timed on this workload (untimed warm-up)
+        from paper_2607_01757_gb300.autotune import autotune
+
+        tcur = [t]
+
+        def tune_step():
+            batched_prepare(tcur[0])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batched_launch(tcur[0])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tcur[0] += 1
+            return e0.elapsed_time(e1)
+
+        best, timings = autotune(tr, tune_step, reps=5, warmup=2)
+        t = tcur[0]
+        tune = {"warps_per_cta": best[0], "ctas_per_sm": best[1] or "occupancy limit",
+                "median_ms": {k: round(statistics.median(v), 4) for k, v in timings.items()}}
     for _ in range(a.warmup):
         batched_step(t)
         t += 1
@@ -586,6 +610,7 @@ def run_native(a, rank, world, local_rank):
             "fb_thr": prm.fb_thr,
             "l2": "flushed between steps (256 MB write outside the per-step CUDA events)",
             "graph": True,
+            "launch_shape": tune,
             "seed": a.seed,
             "parallelism": "replicas" if world > 1 else "single",
         },
@@ -812,7 +837,17 @@ def main():
     if a.small:
         a.streams = min(a.streams, 4)
         a.no_cpu = True
-    if a.impl == "reference":
+    if a.only == "gftt":  # the detector section alone (for profiler captures)
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        specs, frames = make_workload(a.streams, 1, rank_seed(a.seed, rank), os.cpu_count() or 1)
+        if rank == 0:
+            run_gftt(specs, frames)  # first pass: module loading and clock ramp-up
+            res = {"gftt": run_gftt(specs, frames)}
+        else:
+            res = None
+    elif a.impl == "reference":
         res = run_reference(a, rank, world)
     else:
         res = run_native(a, rank, world, local_rank)
