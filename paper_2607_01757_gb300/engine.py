@@ -61,6 +61,13 @@ class BatchedTracker:
         self.grad_type = grad_type
         self.gate = gate
         self.streams = []
+        # every stream's outputs are slices of three contiguous buffers, so one
+        # copy each brings a whole step's results to the host
+        total = sum(sp.n_kp * (2 if sp.stereo else 1) for sp in specs)
+        self.out_pts = torch.zeros((max(1, total), 2), dtype=torch.float32, device=device)
+        self.out_st = torch.zeros(max(1, total), dtype=torch.uint8, device=device)
+        self.out_err = torch.zeros(max(1, total), dtype=torch.float32, device=device)
+        off = 0
         for j, sp in enumerate(specs):
             s = StreamState(sp.sid, sp.w, sp.h, sp.levels, sp.stereo, sp.n_kp)
             s.pyr = [vt.vt_pyramid_create(sp.w, sp.h, sp.levels) for _ in range(2)]
@@ -69,11 +76,14 @@ class BatchedTracker:
             s.in_right = torch.zeros((sp.h, sp.w), dtype=torch.uint8, device=device) if sp.stereo else None
             s.kp_t = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device)
             s.kp_s = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device) if sp.stereo else None
-            mk = lambda: (torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device),  # noqa: E731
-                          torch.zeros(sp.n_kp, dtype=torch.uint8, device=device),
-                          torch.zeros(sp.n_kp, dtype=torch.float32, device=device))
-            s.out_t = mk()
-            s.out_s = mk() if sp.stereo else ()
+            def mk(o, n=sp.n_kp):
+                return self.out_pts[o:o + n], self.out_st[o:o + n], self.out_err[o:o + n]
+
+            s.out_t = mk(off)
+            off += sp.n_kp
+            if sp.stereo:
+                s.out_s = mk(off)
+                off += sp.n_kp
             if gate is not None and sp.stereo:
                 s.rig = rigs[j]
                 s.gate_out = (torch.zeros(sp.n_kp, dtype=torch.uint8, device=device),
