@@ -1,0 +1,48 @@
+"""The benchmark's JSON contract.
+
+CPU: the reference arm (the oracle timed on the host) prints one JSON line
+with the contract's keys.  GPU: a small native run prints one JSON line with
+every key the contract asks for, each section filled in."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+        "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "roofline", "cpu_baseline", "clocks")
+
+
+def _run(args, timeout):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                         timeout=timeout, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = _run(["--impl", "reference", "--steps", "1", "--warmup", "0", "--streams", "2"], 600)
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.gpu
+def test_native_small_run_line():
+    d = _run(["--small", "--steps", "3", "--warmup", "3", "--no-served", "--cpu-seconds", "2"], 900)
+    for k in KEYS:
+        assert k in d, k
+    assert d["value"] > 0 and d["gpu_launches"] > 0 and d["n_gpus"] == 1
+    r = d["roofline"]
+    assert 0 < r["frac"] < 1.5 and r["achieved"] > 0 and r["peak"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["value"] > 0
+    for sec in ("gftt", "stereo_gate", "track_bookkeeping", "frontend_loop", "plain"):
+        assert d[sec], sec
+    assert d["config"]["launch_shape"]["warps_per_cta"] in (4, 8)
