@@ -97,10 +97,12 @@ def test_precision_workload_fp16_gradients_error_stated(precision_seq):
     assert stats["mean"] < 0.005 and stats["p99"] < 0.02 and stats["max"] < 0.05, stats
 
 
-def test_full_size_streams_batched_sampled():
+@pytest.mark.parametrize("warps", [4, 8])
+def test_full_size_streams_batched_sampled(warps):
     """The batched launch of the benchmark on full-size stream shapes (one
     stream of each shape, stereo and mono), every point tracked on the GPU,
-    a sample of 48 points per task re-tracked by the oracle one by one."""
+    a sample of 48 points per task re-tracked by the oracle one by one; with
+    either launch shape the benchmark's tuner can pick (4 or 8 warps per CTA)."""
     import torch
 
     import paper_2607_01757_gb300 as vt
@@ -115,6 +117,7 @@ def test_full_size_streams_batched_sampled():
     frames = [synth.render_stream_frames(sp, 2) for sp in pick]
     prm = vt.KltParams()
     tr = BatchedTracker(pick, prm)
+    vt.vt_batch_config(tr.batch, warps, 0, 0)
     sids = list(range(len(pick)))
     L0 = [torch.from_numpy(f.left[0]).cuda() for f in frames]
     L1 = [torch.from_numpy(f.left[1]).cuda() for f in frames]

@@ -182,3 +182,38 @@ def test_batched_gate_matches_single_calls_and_oracle():
     tr.free()
     # pyramid levels + tail + tracking + gate
     assert launches >= 4
+
+
+def test_batched_gate_general_rigs_without_tracking():
+    """Gate tasks alone in a batched run (no frames, no tracking tasks), each
+    with its own general rig: equal to the oracle under the margin rule and
+    bit-identical to the single call."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    gprm = vt.GateParams(min_disp=0.5, z_min=0.2, z_max=80.0, max_reproj=1.5)
+    prm_o = S.GateParams(0.5, 0.2, 80.0, 1.5)
+    b = vt.Batch(1, 4)
+    vt.vt_batch_set(b, [], [], vt.KltParams())
+    tasks, keep, refs = [], [], []
+    for seed in (21, 22, 23):
+        rig, pl, pr, st = _mixed_pairs(600 + 37 * seed, seed=seed)
+        dl, dr = torch.from_numpy(pl).cuda(), torch.from_numpy(pr).cuda()
+        ds = torch.from_numpy(st).cuda()
+        out = torch.zeros(len(pl), dtype=torch.uint8, device="cuda")
+        xyz = torch.zeros((len(pl), 3), device="cuda")
+        rs = torch.zeros(len(pl), dtype=torch.uint8, device="cuda")
+        vrig = vt.StereoRig(rig.kl, rig.kr, rig.R, rig.t)
+        tasks.append(vt.gate_task(dl, dr, vrig, out, status_in=ds, xyz=xyz, reason=rs))
+        keep.append((dl, dr, ds, out, xyz, rs, vrig, pl, pr, st, rig))
+    vt.vt_batch_set_gates(b, tasks, gprm)
+    vt.vt_batch_run(b)
+    torch.cuda.synchronize()
+    for dl, dr, ds, out, xyz, rs, vrig, pl, pr, st, rig in keep:
+        r = S.stereo_gate(pl, pr, st, rig, prm_o)
+        _compare((xyz.cpu().numpy(), out.cpu().numpy(), rs.cpu().numpy()), r, "batched general rig")
+        g = _gpu_gate(pl, pr, st, rig, prm_o)
+        assert np.array_equal(g[1], out.cpu().numpy()) and np.array_equal(g[2], rs.cpu().numpy())
+        assert np.array_equal(g[0].view(np.uint32), xyz.cpu().numpy().view(np.uint32))
+    b.free()
