@@ -395,7 +395,9 @@ VT_API vt_status vt_tracks_spawn(const vt_spawn_job *jobs, int njobs, void *cuda
  * ---------------------------------------------------------------------- */
 
 /* Build pyramid `pyr` (levels and gradients) from the device image `img`
- * (the pyramid's w x h, `pitch` bytes per row, any alignment). */
+ * (the pyramid's w x h, `pitch` bytes per row, any alignment; pinned host
+ * memory also works -- the kernels then read it over the host link, which is
+ * slower than copying it first). */
 typedef struct vt_frame_job {
     const uint8_t *img;
     int pitch;

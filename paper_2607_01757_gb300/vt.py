@@ -363,10 +363,11 @@ def vt_batch_config(b: Batch, klt_warps_per_cta: int = 4, klt_ctas_per_sm: int =
 
 
 def frame_job(img, pyr: Pyramid) -> vt_frame_job:
-    """Descriptor of one pyramid build from a 2-D uint8 device tensor."""
+    """Descriptor of one pyramid build from a 2-D uint8 device tensor, or a
+    pinned host tensor (the pyramid kernel then reads it over the host link)."""
     p, w, h, pitch, dev = _img_args(img)
-    if not dev:
-        raise ValueError("batched frames must be device images")
+    if not dev and not (hasattr(img, "is_pinned") and img.is_pinned()):
+        raise ValueError("batched frames must be device images or pinned host tensors")
     return vt_frame_job(p, pitch, pyr.handle)
 
 
