@@ -72,11 +72,12 @@ struct KltBatchKernel {
 template <int WIN, int GT, int WARPS>
 static KltBatchKernel klt_batch_entry() {
     const size_t smem = WARPS * sizeof(KSmem<WIN>);
-    static bool attr = false;
-    if (!attr) {  // opt in to more than 48 KB where needed (idempotent)
-        cudaFuncSetAttribute(k_klt_batch<WIN, GT, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // opt in to more than 48 KB where needed (once, thread-safe static initialisation)
+    static const bool attr = [smem] {
+        return cudaFuncSetAttribute(k_klt_batch<WIN, GT, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) == cudaSuccess;
+    }();
+    (void)attr;
     return {k_klt_batch<WIN, GT, WARPS>, smem};
 }
 

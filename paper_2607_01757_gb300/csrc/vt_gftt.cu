@@ -841,13 +841,13 @@ vt_status vt_gftt_detect_many(vt_gftt *g, const vt_gftt_job *jobs, int njobs, co
         cudaGetLastError();
         return VT_ERR_CUDA;
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gftt_output, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(GF_SMEM_SORT * sizeof(unsigned long long)));
-        cudaFuncSetAttribute(k_gftt_greedy_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GreedySmem));
-        attr = true;
-    }
+    static const bool attr = [] {  // once, thread-safe static initialisation
+        return cudaFuncSetAttribute(k_gftt_output, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(GF_SMEM_SORT * sizeof(unsigned long long))) == cudaSuccess &&
+               cudaFuncSetAttribute(k_gftt_greedy_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(GreedySmem)) == cudaSuccess;
+    }();
+    (void)attr;
     const dim3 blk(GF_TX, GF_TY);
     int max_mask = 0;
     for (int i = 0; i < njobs; ++i) max_mask = max(max_mask, jobs[i].n_mask);

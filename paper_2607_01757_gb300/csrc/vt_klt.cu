@@ -62,11 +62,11 @@ static vt_status launch_one(const KltArgs &A, cudaStream_t s) {
     const int blocks = (A.n + KLT_WARPS - 1) / KLT_WARPS;
     const size_t smem = KLT_WARPS * sizeof(KSmem<WIN>);
     if (smem > 48 * 1024) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_klt<WIN, GT, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
+        static const bool attr = [smem] {  // once, thread-safe static initialisation
+            return cudaFuncSetAttribute(k_klt<WIN, GT, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem) == cudaSuccess;
+        }();
+        (void)attr;
     }
     k_klt<WIN, GT, FB><<<blocks, KLT_WARPS * 32, smem, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;

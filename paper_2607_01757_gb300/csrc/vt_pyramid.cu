@@ -533,13 +533,15 @@ __host__ __device__ int scharr_tiles(int w, int h, int &tiles_x) {
 
 vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,
                            cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_S16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
-        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
-        cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TAIL_SMEM);
-        attr = true;
-    }
+    static const bool attr = [] {  // once, thread-safe static initialisation
+        return cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_S16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TAIL_SMEM) == cudaSuccess &&
+               cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TAIL_SMEM) == cudaSuccess &&
+               cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    TAIL_SMEM) == cudaSuccess;
+    }();
+    (void)attr;
     for (int l = 0; l < tiled_launches; ++l) {
         if (gtype == VT_GRAD_F16)
             k_pyr_batch<VT_GRAD_F16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);

@@ -332,11 +332,11 @@ vt_status vt_tracks_carry(const vt_carry_job *jobs, int njobs, float min_dist, v
     J.n = njobs;
     J.min_dist = min_dist;
     for (int i = 0; i < njobs; ++i) J.j[i] = jobs[i];
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_tracks_carry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CarrySmem));
-        attr = true;
-    }
+    static const bool attr = [] {  // once, thread-safe static initialisation
+        return cudaFuncSetAttribute(k_tracks_carry, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(CarrySmem)) == cudaSuccess;
+    }();
+    (void)attr;
     k_tracks_carry<<<njobs, TK_THREADS, sizeof(CarrySmem), (cudaStream_t)cuda_stream>>>(J);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
