@@ -166,6 +166,7 @@ __global__ void k_gftt_mask(const __grid_constant__ GJobs J, uint8_t *masked) {
 // smaller index wins the tie) and not masked goes to the frame's list of
 // local maxima.  The quality threshold, which needs the frame maximum, is
 // applied afterwards (k_gftt_filter).
+template <int BR>  // block radius: the box-sum taps unroll with constant offsets
 __global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_local(const __grid_constant__ GJobs J, GCount *cnt,
                                                              const uint8_t *masked, unsigned long long *lmax) {
     constexpr int HG = GF_MAX_NMS + GF_MAX_BR;
@@ -176,7 +177,8 @@ __global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_local(const __grid_consta
     const int jb = tile_job(J, blockIdx.x);
     const GJob &G = J.j[jb];
     const int t = blockIdx.x - G.tile0, ty = t / G.tiles_x, tx = t - ty * G.tiles_x;
-    const int x0 = tx * GF_TX, y0 = ty * GF_TY, nms = J.nms, br = J.br, hg = nms + br;
+    constexpr int br = BR;
+    const int x0 = tx * GF_TX, y0 = ty * GF_TY, nms = J.nms, hg = nms + br;
     const int tid = threadIdx.y * GF_TX + threadIdx.x;
     const int gw = GF_TX + 2 * hg, gh = GF_TY + 2 * hg;
     const bool interior = x0 - hg >= 0 && y0 - hg >= 0 && x0 + GF_TX + hg <= G.w && y0 + GF_TY + hg <= G.h;
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(GF_TX *GF_TY) k_gftt_local(const __grid_consta
         float v = -1.0f;
         if (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) {
             int a = 0, b = 0, cc = 0;  // at most 49 * 4080^2 < 2^31
+#pragma unroll
             for (int j = 0; j <= 2 * br; ++j)
+#pragma unroll
                 for (int k = 0; k <= 2 * br; ++k) {
                     const uint32_t g = sg[r + j][c + k];
                     const int u = (int16_t)(g & 0xffffu), w = (int16_t)(g >> 16);
@@ -859,7 +863,12 @@ vt_status vt_gftt_detect_many(vt_gftt *g, const vt_gftt_job *jobs, int njobs, co
         const dim3 mgrid((unsigned)min(1024, (max_mask + 7) / 8), (unsigned)njobs);
         k_gftt_mask<<<mgrid, 256, 0, s>>>(J, g->state);
     }
-    k_gftt_local<<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys);
+    switch (prm->block_radius) {
+        case 0: k_gftt_local<0><<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys); break;
+        case 1: k_gftt_local<1><<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys); break;
+        case 2: k_gftt_local<2><<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys); break;
+        default: k_gftt_local<3><<<tiles, blk, 0, s>>>(J, g->cnt, g->state, g->skeys); break;
+    }
     const dim3 cgrid((unsigned)((4 * g->sms + njobs - 1) / njobs), (unsigned)njobs);
     k_gftt_filter<<<cgrid, GF_GRID_THREADS, 0, s>>>(J, g->cnt, g->skeys, g->keys);
     k_gftt_hist<<<cgrid, GF_GRID_THREADS, 0, s>>>(J, g->cnt, g->keys, g->hist);
