@@ -800,6 +800,29 @@ def run_gftt(specs, frames):
     return out
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its core count."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        name = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({os.cpu_count()} cores)"
+
+
 def cpu_baseline(specs, frames, prm, seconds):
     """The FP64 oracle, single-threaded, on a bounded sample of step 1 of the
     same workload: pyramids + Scharr of the frames it needs, then the
@@ -832,7 +855,7 @@ def cpu_baseline(specs, frames, prm, seconds):
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": feats / dt, "unit": "features/s", "cores": 1, "kind": "oracle",
+    return {"value": feats / dt, "unit": "features/s", "cores": 1, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"step 1 of the same workload: {feats} features of {streams} stream(s) incl. their pyramids, "
                       f"FP64 single-threaded C, {dt:.1f} s"}
 
@@ -882,7 +905,7 @@ def run_reference(a, rank, world):
                                "(temporal + stereo FB tracking, pyramids included)", "streams": len(specs)},
         "latency_ms": {"p50": times[len(times) // 2] * 1e3, "p99": times[min(len(times) - 1,
                                                                               int(0.99 * len(times)))] * 1e3},
-        "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "cpu": cpu_model(), "kind": "oracle",
                          "sample": "128 keypoints of one stream per step"},
         "e2e": {"value": v, "unit": "features/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
