@@ -147,3 +147,39 @@ def test_full_size_streams_batched_sampled(warps):
             compare(out[0].cpu().numpy()[idx], out[1].cpu().numpy()[idx], r.fwd.pts, r.status, oracle_margin(r),
                     f"{sp.w}x{sp.h} L{sp.levels}")
     tr.free()
+
+
+def test_stereo_temporal_sequence_six_frames_batched():
+    """The stereo + temporal sequence stepped frame by frame through the
+    batched engine (one stereo stream, 752x480, 1000 keypoints per frame,
+    5 levels): at every step prev->cur and left->right tracking of a sample
+    of 120 points agree with the oracle."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.engine import BatchedTracker
+
+    F = 6
+    seq = synth.make_stereo_sequence(seed=2, n_frames=F, w=752, h=480, n_kp=1000)
+    spec = synth.StreamSpec(sid=0, w=752, h=480, stereo=True, n_kp=1000, levels=5, seed=2)
+    tr = BatchedTracker([spec], vt.KltParams(win=21, levels=5))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    rng = np.random.Generator(np.random.PCG64(31))
+    for t in range(F):
+        L, R = dev(seq.left[t]), dev(seq.right[t])
+        n_t = len(seq.kps[t - 1]) if t > 0 else 0
+        kt = dev(seq.kps[t - 1]) if t > 0 else dev(seq.kps[0])
+        tr.stage(tr.step_tables([0], [n_t], [len(seq.kps[t])], [L], [R], kpt=[kt], kps=[dev(seq.kps[t])]))
+        tr.run(graph=True)
+        tr.advance([0])
+        torch.cuda.synchronize()
+        s = tr.streams[0]
+        tasks = [(seq.left[t], seq.right[t], seq.kps[t], s.out_s, "stereo")]
+        if t > 0:
+            tasks.append((seq.left[t - 1], seq.left[t], seq.kps[t - 1], s.out_t, "temporal"))
+        for I, J, kp, out, label in tasks:
+            idx = np.sort(rng.choice(len(kp), size=120, replace=False))
+            r = _oracle_fb(I, J, kp[idx], vt.KltParams(win=21, levels=5))
+            compare(out[0].cpu().numpy()[idx], out[1].cpu().numpy()[idx], r.fwd.pts, r.status, oracle_margin(r),
+                    f"frame {t} {label}")
+    tr.free()
