@@ -101,3 +101,29 @@ def test_stereo_gate_argument_errors_need_no_device():
     with pytest.raises(vt.VTError):
         f(np.zeros((3, 2), np.float32), np.zeros((3, 2), np.float32), rig, vt.GateParams(min_disp=-2.0),
           np.zeros(3, np.uint8), stream=0)
+
+
+def test_bookkeeping_and_detector_argument_errors_need_no_device():
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.vt import _lib as lib
+
+    one = C.c_void_p(16)
+    pool = vt.vt_track_pool(one, one, one, one, one, 100)
+    job = vt.vt_carry_job(pool, one, one, None)
+    jobs = (vt.vt_carry_job * 1)(job)
+    assert lib.vt_tracks_carry(jobs, 0, C.c_float(8.0), None) == vt.VT_OK  # nothing to do
+    assert lib.vt_tracks_carry(jobs, -1, C.c_float(8.0), None) == vt.VT_ERR_ARG
+    assert lib.vt_tracks_carry(jobs, 1, C.c_float(0.0), None) == vt.VT_ERR_ARG  # min_dist must be > 0
+    assert lib.vt_tracks_carry(jobs, 1, C.c_float(float("nan")), None) == vt.VT_ERR_ARG
+    assert lib.vt_tracks_carry(jobs, 193, C.c_float(8.0), None) == vt.VT_ERR_ARG  # more jobs than one launch holds
+    for bad_cap in (0, vt.VT_POOL_MAX + 1):
+        bad = (vt.vt_carry_job * 1)(vt.vt_carry_job(vt.vt_track_pool(one, one, one, one, one, bad_cap), one, one,
+                                                    None))
+        assert lib.vt_tracks_carry(bad, 1, C.c_float(8.0), None) == vt.VT_ERR_ARG
+    nop = (vt.vt_carry_job * 1)(vt.vt_carry_job(pool, None, one, None))
+    assert lib.vt_tracks_carry(nop, 1, C.c_float(8.0), None) == vt.VT_ERR_ARG  # no tracked positions
+    sj = (vt.vt_spawn_job * 1)(vt.vt_spawn_job(pool, None, one, None))
+    assert lib.vt_tracks_spawn(sj, 1, None) == vt.VT_ERR_ARG  # no corners
+    prm = vt.GfttParams().c()
+    gj = (vt.vt_gftt_job * 1)()
+    assert lib.vt_gftt_detect_many(None, gj, 1, C.byref(prm), None) == vt.VT_ERR_ARG
