@@ -393,19 +393,28 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         // lambda_min = det / lambda_max avoids the cancellation of (tr - disc) / 2
         const float tr = g11 + g22, df = g11 - g22;
         const float lmax = 0.5f * (tr + sqrtf(fmaf(df, df, 4.f * g12 * g12)));
-        const double det = (double)g11 * (double)g22 - (double)g12 * (double)g12;
-        const float lmin = (float)(det / (double)lmax);
+        // det = g11 g22 - g12^2 by Kahan's FMA scheme: w = g12^2 rounded, its
+        // rounding error e = g12^2 - w is exact, det = round(g11 g22 - w) - e.
+        // Relative error at most 2 ulp (Jeannerod, Louvet & Muller, Math. Comp.
+        // 82, 2013) and the sign is exact, all on the FP32 pipes: this GPU's
+        // FP64 pipe retires about 2 lanes per clock per SM, so an FP64
+        // product and divide per template kept it 42 % busy.
+        const float w12 = g12 * g12;
+        const float e12 = fmaf(g12, g12, -w12);
+        const float det = fmaf(g11, g22, -w12) - e12;
+        const float lmin = det / lmax;
         o.lmin = lmin * inv_norm;
         nux = nuy = 0.f;
-        if (!(o.lmin >= P.min_eig) || !(det > 0.0)) {
+        if (!(o.lmin >= P.min_eig) || !(det > 0.f)) {
             o.status = 0;
             o.reason = VT_LOST_EIG;
             lost_level = l;
             break;
         }
         // eta = G^-1 b in grey/px units: G = unit^2 G_s, b = unit b_s => eta = adj(G_s) b_s / (unit det_s)
+        // (unit is a power of two, so det * unit is exact)
         const bool fp64 = lmax > 1e5f * lmin;
-        const float inv_det = (float)(1.0 / (det * (double)unit));
+        const float inv_det = 1.0f / (det * unit);
         // moments of the footprint cell last swept (valid while the integer
         // part of q does not change)
         int cx = INT_MIN, cy = INT_MIN;
@@ -435,7 +444,10 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
                 ex = (g22 * b1 - g12 * b2) * inv_det;
                 ey = (g11 * b2 - g12 * b1) * inv_det;
             } else {
-                const double dd = det * (double)unit;
+                // ill-conditioned G (the normalised lambda_max is at most 0.5,
+                // so only reached with min_eig < 5e-6): exact determinant and
+                // quotients in FP64
+                const double dd = ((double)g11 * (double)g22 - (double)g12 * (double)g12) * (double)unit;
                 ex = (float)(((double)g22 * b1 - (double)g12 * b2) / dd);
                 ey = (float)(((double)g11 * b2 - (double)g12 * b1) / dd);
             }
