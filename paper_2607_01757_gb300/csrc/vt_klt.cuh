@@ -91,6 +91,17 @@ __device__ __forceinline__ void unpack_grad(uint32_t v, float &gx, float &gy) {
 template <int GT>
 __device__ __forceinline__ constexpr float grad_unit() { return GT == VT_GRAD_F16 ? 1.0f : 0.03125f; }
 
+// a b - c d by Kahan's FMA scheme: w = c d rounded, its rounding error
+// c d - w is exact (one FMA), and the result is round(a b - w) minus that
+// error.  Relative error at most 2 ulp and the sign exact (Jeannerod, Louvet
+// & Muller, Math. Comp. 82, 2013) -- as good as FP64 products rounded to FP32,
+// but on the FP32 pipes: this GPU's FP64 pipe retires about 2 lanes per clock
+// per SM, and an FP64 determinant and divides per template kept it 42 % busy.
+__device__ __forceinline__ float kdiff(float a, float b, float c, float d) {
+    const float w = c * d;
+    return fmaf(a, b, -w) - fmaf(c, d, -w);
+}
+
 // 2^-l exactly.
 __device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
 
@@ -237,9 +248,10 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
 }
 
 // Stage the (win + 1) x (win + 1) footprint of J with top-left (x0, y0) in
-// shared memory: 32-bit loads when it lies inside the image, byte loads with
-// clamped (replicated) indices near the border.  Returns the byte offset of
-// column 0 within a staged row.
+// shared memory: 4-byte cp.async copies (global to shared, no register round
+// trip) when it lies inside the image, byte loads with clamped (replicated)
+// indices near the border.  Returns the byte offset of column 0 within a
+// staged row.
 template <int WIN>
 __device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, int lane, KSmem<WIN> &sm) {
     constexpr int NW = KSmem<WIN>::NW, JS = KSmem<WIN>::JS;
@@ -249,11 +261,13 @@ __device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, i
         const int wx0 = x0 & ~3;
         off = x0 - wx0;
         const uint8_t *base = L.img + (size_t)y0 * L.pitch + wx0;
+        const uint32_t sb = (uint32_t)__cvta_generic_to_shared(sm.j);
         for (int k = lane; k < (WIN + 1) * NW; k += 32) {
             const int row = k / NW, wc = k - row * NW;
-            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(base + (size_t)row * L.pitch) + wc);
-            *reinterpret_cast<uint32_t *>(&sm.j[row * JS + 4 * wc]) = w;
+            const uint32_t *g = reinterpret_cast<const uint32_t *>(base + (size_t)row * L.pitch) + wc;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + row * JS + 4 * wc), "l"(g) : "memory");
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else {
         off = 0;
         for (int k = lane; k < (WIN + 1) * (WIN + 1); k += 32) {
@@ -393,15 +407,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         // lambda_min = det / lambda_max avoids the cancellation of (tr - disc) / 2
         const float tr = g11 + g22, df = g11 - g22;
         const float lmax = 0.5f * (tr + sqrtf(fmaf(df, df, 4.f * g12 * g12)));
-        // det = g11 g22 - g12^2 by Kahan's FMA scheme: w = g12^2 rounded, its
-        // rounding error e = g12^2 - w is exact, det = round(g11 g22 - w) - e.
-        // Relative error at most 2 ulp (Jeannerod, Louvet & Muller, Math. Comp.
-        // 82, 2013) and the sign is exact, all on the FP32 pipes: this GPU's
-        // FP64 pipe retires about 2 lanes per clock per SM, so an FP64
-        // product and divide per template kept it 42 % busy.
-        const float w12 = g12 * g12;
-        const float e12 = fmaf(g12, g12, -w12);
-        const float det = fmaf(g11, g22, -w12) - e12;
+        const float det = kdiff(g11, g22, g12, g12);  // sign exact, 2 ulp
         const float lmin = det / lmax;
         o.lmin = lmin * inv_norm;
         nux = nuy = 0.f;
@@ -412,8 +418,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             break;
         }
         // eta = G^-1 b in grey/px units: G = unit^2 G_s, b = unit b_s => eta = adj(G_s) b_s / (unit det_s)
-        // (unit is a power of two, so det * unit is exact)
-        const bool fp64 = lmax > 1e5f * lmin;
+        // (unit is a power of two, so det * unit is exact; the adjugate
+        // products cancel for ill-conditioned G, hence kdiff)
         const float inv_det = 1.0f / (det * unit);
         // moments of the footprint cell last swept (valid while the integer
         // part of q does not change)
@@ -439,18 +445,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             const float bx = qx - fx, by = qy - fy, bxy = bx * by;
             const float b1 = m[0] - bx * m[1] - by * m[2] - bxy * m[3];
             const float b2 = m[4] - bx * m[5] - by * m[6] - bxy * m[7];
-            float ex, ey;
-            if (!fp64) {
-                ex = (g22 * b1 - g12 * b2) * inv_det;
-                ey = (g11 * b2 - g12 * b1) * inv_det;
-            } else {
-                // ill-conditioned G (the normalised lambda_max is at most 0.5,
-                // so only reached with min_eig < 5e-6): exact determinant and
-                // quotients in FP64
-                const double dd = ((double)g11 * (double)g22 - (double)g12 * (double)g12) * (double)unit;
-                ex = (float)(((double)g22 * b1 - (double)g12 * b2) / dd);
-                ey = (float)(((double)g11 * b2 - (double)g12 * b1) / dd);
-            }
+            const float ex = kdiff(g22, b1, g12, b2) * inv_det;
+            const float ey = kdiff(g11, b2, g12, b1) * inv_det;
             nux += ex;
             nuy += ey;
             ++o.iters;
