@@ -106,11 +106,13 @@ __device__ __forceinline__ float kdiff(float a, float b, float c, float d) {
 __device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
 
 // Per-warp shared scratch: the staged footprint of J for one window sweep
-// (win + 1 rows of NW 32-bit words).
+// (win + 1 rows of NC 16-byte chunks).
 template <int WIN>
 struct KSmem {
-    static constexpr int NW = (WIN + 7) / 4;            // words per staged row: covers 3 + win + 1 bytes
-    static constexpr int JS = (NW * 4 + 15) / 16 * 16;  // staged row stride in bytes
+    static constexpr int NC = (WIN + 31) / 16;  // 16-byte chunks per staged row: cover 15 + win + 1 bytes
+    static constexpr int JS = NC * 16;          // staged row stride in bytes
+    static_assert(JS >= 15 + WIN + 1 && JS - 1 - WIN <= 32, "a staged row covers the footprint row and reads "
+                                                              "at most 32 bytes past it (the allocation keeps 256)");
     uint8_t j[(WIN + 1) * JS];
 };
 
@@ -248,24 +250,26 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
 }
 
 // Stage the (win + 1) x (win + 1) footprint of J with top-left (x0, y0) in
-// shared memory: 4-byte cp.async copies (global to shared, no register round
-// trip) when it lies inside the image, byte loads with clamped (replicated)
+// shared memory: 16-byte cp.async copies of whole aligned chunks (global to
+// shared, no register round trip) when it lies inside the image -- they may
+// read up to 26 bytes (window 21) past a row's last pixel, inside the level's pitch or
+// the pyramid allocation's slack -- and byte loads with clamped (replicated)
 // indices near the border.  Returns the byte offset of column 0 within a
 // staged row.
 template <int WIN>
 __device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, int lane, KSmem<WIN> &sm) {
-    constexpr int NW = KSmem<WIN>::NW, JS = KSmem<WIN>::JS;
+    constexpr int NC = KSmem<WIN>::NC, JS = KSmem<WIN>::JS;
     int off;
     __syncwarp();  // every lane is done with the previous footprint
     if (x0 >= 0 && y0 >= 0 && x0 + WIN < L.w && y0 + WIN < L.h) {
-        const int wx0 = x0 & ~3;
+        const int wx0 = x0 & ~15;
         off = x0 - wx0;
         const uint8_t *base = L.img + (size_t)y0 * L.pitch + wx0;
         const uint32_t sb = (uint32_t)__cvta_generic_to_shared(sm.j);
-        for (int k = lane; k < (WIN + 1) * NW; k += 32) {
-            const int row = k / NW, wc = k - row * NW;
-            const uint32_t *g = reinterpret_cast<const uint32_t *>(base + (size_t)row * L.pitch) + wc;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sb + row * JS + 4 * wc), "l"(g) : "memory");
+        for (int k = lane; k < (WIN + 1) * NC; k += 32) {
+            const int row = k / NC, wc = k - row * NC;
+            const uint8_t *g = base + (size_t)row * L.pitch + 16 * wc;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sb + row * JS + 16 * wc), "l"(g) : "memory");
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else {
