@@ -250,34 +250,37 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
 }
 
 // Stage the (win + 1) x (win + 1) footprint of J with top-left (x0, y0) in
-// shared memory: 16-byte cp.async copies of whole aligned chunks (global to
-// shared, no register round trip) when it lies inside the image -- they may
-// read up to 26 bytes (window 21) past a row's last pixel, inside the level's pitch or
-// the pyramid allocation's slack -- and byte loads with clamped (replicated)
-// indices near the border.  Returns the byte offset of column 0 within a
-// staged row.
+// shared memory, rows and columns clamped into the image (replicate).  When
+// its columns lie inside the image, each (clamped) row is copied in whole
+// aligned 16-byte chunks by cp.async (global to shared, no register round
+// trip); they may read up to 26 bytes (window 21) past a row's last pixel,
+// inside the level's pitch or the pyramid allocation's slack.  Otherwise lane
+// c loads column c (clamped) of every row.  Returns the byte offset of column
+// 0 within a staged row.
 template <int WIN>
 __device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, int lane, KSmem<WIN> &sm) {
     constexpr int NC = KSmem<WIN>::NC, JS = KSmem<WIN>::JS;
     int off;
     __syncwarp();  // every lane is done with the previous footprint
-    if (x0 >= 0 && y0 >= 0 && x0 + WIN < L.w && y0 + WIN < L.h) {
+    if (x0 >= 0 && x0 + WIN < L.w) {
         const int wx0 = x0 & ~15;
         off = x0 - wx0;
-        const uint8_t *base = L.img + (size_t)y0 * L.pitch + wx0;
+        const uint8_t *base = L.img + wx0;
+        const int hm1 = L.h - 1;
         const uint32_t sb = (uint32_t)__cvta_generic_to_shared(sm.j);
         for (int k = lane; k < (WIN + 1) * NC; k += 32) {
             const int row = k / NC, wc = k - row * NC;
-            const uint8_t *g = base + (size_t)row * L.pitch + 16 * wc;
+            const uint8_t *g = base + (size_t)clampi(y0 + row, 0, hm1) * L.pitch + 16 * wc;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sb + row * JS + 16 * wc), "l"(g) : "memory");
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else {
         off = 0;
-        for (int k = lane; k < (WIN + 1) * (WIN + 1); k += 32) {
-            const int row = k / (WIN + 1), c = k - row * (WIN + 1);
-            sm.j[row * JS + c] = __ldg(L.img + (size_t)clampi(y0 + row, 0, L.h - 1) * L.pitch +
-                                       clampi(x0 + c, 0, L.w - 1));
+        if (lane <= WIN) {
+            const uint8_t *col = L.img + clampi(x0 + lane, 0, L.w - 1);
+            const int hm1 = L.h - 1;
+#pragma unroll
+            for (int r = 0; r <= WIN; ++r) sm.j[r * JS + lane] = __ldg(col + (size_t)clampi(y0 + r, 0, hm1) * L.pitch);
         }
     }
     __syncwarp();
@@ -394,8 +397,9 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         gy = (guy - uy0) * s;
     }
     for (int l = L - 1; l >= 0; --l) {
-        const Level &Il = I[l];
-        const Level &Jl = J[l];
+        // by value: the fields stay in registers across the staging copies
+        const Level Il = I[l];
+        const Level Jl = J[l];
         const float s = pow2neg(l);
         const float ux = ux0 * s, uy = uy0 * s;
         load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY);
