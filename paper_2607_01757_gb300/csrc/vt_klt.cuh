@@ -21,8 +21,9 @@
 // iterations that stay in the same cell reuse the moments.  The template and
 // its gradients stay in registers (3 * win floats per lane); the footprint is
 // staged in per-warp shared memory.  Sums over the window are per-lane FP32
-// sums over rows followed by an XOR butterfly, so every lane holds
-// bit-identical totals and control flow stays warp-uniform.
+// sums over rows followed by a warp reduction that leaves bit-identical
+// totals in every lane (an XOR butterfly, or a reduce-scatter and broadcast),
+// so control flow stays warp-uniform.
 #pragma once
 
 #include <climits>
@@ -67,6 +68,50 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
     return v;
+}
+
+// Warp totals of eight per-lane values, delivered to every lane: the three
+// top butterfly levels are a reduce-scatter (each halves the set a lane
+// carries), the last two reduce the lane's single value, and the eight totals
+// are broadcast from lanes 0, 4, .., 28.  17 shuffles instead of 5 x 8.
+__device__ __forceinline__ void warp_sum8(const float (&a)[8], int lane, float (&m)[8]) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float b[4], c[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = h16 ? a[k] : a[k + 4], keep = h16 ? a[k + 4] : a[k];
+        b[k] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = h8 ? b[k] : b[k + 2], keep = h8 ? b[k + 2] : b[k];
+        c[k] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    const float send = h4 ? c[0] : c[1], keep = h4 ? c[1] : c[0];
+    float d = keep + __shfl_xor_sync(kFull, send, 4);
+    d += __shfl_xor_sync(kFull, d, 2);
+    d += __shfl_xor_sync(kFull, d, 1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = __shfl_sync(kFull, d, 4 * k);  // lane 4k holds total k
+}
+
+// Warp totals of three per-lane values the same way (the set padded to four
+// with a zero; totals broadcast from lanes 0, 8, 16): 9 shuffles instead of
+// 5 x 3.
+__device__ __forceinline__ void warp_sum3(float x, float y, float z, int lane, float &sx, float &sy, float &sz) {
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const float s0 = h16 ? x : z, k0 = h16 ? z : x;
+    const float s1 = h16 ? y : 0.f, k1 = h16 ? 0.f : y;
+    const float b0 = k0 + __shfl_xor_sync(kFull, s0, 16);
+    const float b1 = k1 + __shfl_xor_sync(kFull, s1, 16);
+    const float sd = h8 ? b0 : b1, kd = h8 ? b1 : b0;
+    float d = kd + __shfl_xor_sync(kFull, sd, 8);
+    d += __shfl_xor_sync(kFull, d, 4);
+    d += __shfl_xor_sync(kFull, d, 2);
+    d += __shfl_xor_sync(kFull, d, 1);
+    sx = __shfl_sync(kFull, d, 0);
+    sy = __shfl_sync(kFull, d, 8);
+    sz = __shfl_sync(kFull, d, 16);
 }
 
 // 2^23 + v as a float for a byte v: differences of two such values are exact.
@@ -330,8 +375,7 @@ __device__ __forceinline__ void cell_moments(const Level &L, int x0, int y0, int
         pmv = mv;
         pdx = dx;
     }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) m[k] = warp_sum(a[k]);
+    warp_sum8(a, lane, m);
 }
 
 // Error sweep at (qx, qy): sum |T - J_l(q + x)| over the window.
@@ -411,7 +455,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
             a12 = fmaf(GX[r], GY[r], a12);
             a22 = fmaf(GY[r], GY[r], a22);
         }
-        const float g11 = warp_sum(a11), g12 = warp_sum(a12), g22 = warp_sum(a22);
+        float g11, g12, g22;
+        warp_sum3(a11, a12, a22, lane, g11, g12, g22);
         // lambda_min = det / lambda_max avoids the cancellation of (tr - disc) / 2
         const float tr = g11 + g22, df = g11 - g22;
         const float lmax = 0.5f * (tr + sqrtf(fmaf(df, df, 4.f * g12 * g12)));
