@@ -114,9 +114,10 @@ __device__ __forceinline__ void warp_sum3(float x, float y, float z, int lane, f
     sz = __shfl_sync(kFull, d, 16);
 }
 
-// 2^23 + v as a float for a byte v: differences of two such values are exact.
-__device__ __forceinline__ float magic_u8(uint32_t v) { return __uint_as_float(0x4B000000u | v); }
-constexpr float kMagic = 8388608.0f;
+// A byte as a float (exact; differences of two are exact integers).  The
+// conversion runs on its own pipe, off the integer pipe that an OR-with-2^23
+// conversion would load.
+__device__ __forceinline__ float u8f(uint32_t v) { return __uint2float_rn(v); }
 
 template <int GT>
 __device__ __forceinline__ void unpack_grad(uint32_t v, float &gx, float &gy) {
@@ -217,7 +218,7 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
         const int dd = top ? dt : (bot ? db : dp), sd = top ? st : (bot ? sb : sp);
         const float gx = (float)(3 * (du + dd) + 10 * d0);
         const float gy = (float)(sd - su);
-        const float mv = magic_u8((uint32_t)c0);
+        const float mv = u8f((uint32_t)c0);
         dm = d0;
         sm_m = s0;
         d0 = dp;
@@ -226,7 +227,7 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
         const float mvr = __shfl_down_sync(kFull, mv, 1);
         const float gxr = __shfl_down_sync(kFull, gx, 1);
         const float gyr = __shfl_down_sync(kFull, gy, 1);
-        const float hi = fmaf(ax, mvr - mv, mv - kMagic);
+        const float hi = fmaf(ax, mvr - mv, mv);
         const float hgx = fmaf(ax, gxr - gx, gx);
         const float hgy = fmaf(ax, gyr - gy, gy);
         if (r > 0) {
@@ -270,13 +271,13 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
             v = __ldg(ib + (size_t)row * L.pitch);
             g = __ldg(gb + (size_t)row * L.gpitch);
         }
-        const float mv = magic_u8(v);
+        const float mv = u8f(v);
         const float mvr = __shfl_down_sync(kFull, mv, 1);
         float gx, gy;
         unpack_grad<GT>(g, gx, gy);
         const float gxr = __shfl_down_sync(kFull, gx, 1);
         const float gyr = __shfl_down_sync(kFull, gy, 1);
-        const float hi = fmaf(ax, mvr - mv, mv - kMagic);
+        const float hi = fmaf(ax, mvr - mv, mv);
         const float hgx = fmaf(ax, gxr - gx, gx);
         const float hgy = fmaf(ax, gyr - gy, gy);
         if (r > 0) {
@@ -355,11 +356,11 @@ __device__ __forceinline__ void cell_moments(const Level &L, int x0, int y0, int
     float pmv = 0.f, pdx = 0.f;
 #pragma unroll
     for (int r = 0; r <= WIN; ++r) {
-        const float mv = magic_u8(jr[r * JS]);
+        const float mv = u8f(jr[r * JS]);
         const float mvr = __shfl_down_sync(kFull, mv, 1);
         const float dx = mvr - mv;  // F(r, c+1) - F(r, c), exact
         if (r > 0) {
-            const float e0 = T[r - 1] - (pmv - kMagic);
+            const float e0 = T[r - 1] - pmv;
             const float sy = mv - pmv;   // F10 - F00
             const float sxy = dx - pdx;  // F11 - F10 - F01 + F00
             const float gx = GX[r - 1], gy = GY[r - 1];
@@ -390,9 +391,9 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
     float sa = 0.f, sb = 0.f, ph = 0.f;
 #pragma unroll
     for (int r = 0; r <= WIN; ++r) {
-        const float mv = magic_u8(jr[r * JS]);
+        const float mv = u8f(jr[r * JS]);
         const float mvr = __shfl_down_sync(kFull, mv, 1);
-        const float h = fmaf(bx, mvr - mv, mv - kMagic);
+        const float h = fmaf(bx, mvr - mv, mv);
         if (r > 0) {
             const float jv = fmaf(by, h - ph, ph);
             const float e = (lane < WIN) ? fabsf(T[r - 1] - jv) : 0.f;
