@@ -35,10 +35,11 @@ L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 # DRAM bytes (read + write) per launch from one ncu capture of the default
-# workload (32 streams, 4 frames, seed 4; dram__bytes_read.sum +
-# dram__bytes_write.sum, caches flushed before each captured launch), summarised
-# in profiles/launches_bench_32streams.md.  Reported only for that workload.
-NCU_TRAFFIC_BYTES = {"k_klt_batch": 431.18e6 + 0.87e6, "pyramid": 83.2e6 + 271.4e6}
+# workload with the current kernels (32 streams, 4 frames, seed 4;
+# dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before each
+# captured launch, mean of two captured steps), summarised in
+# profiles/launches_bench_32streams.md.  Reported only for that workload.
+NCU_TRAFFIC_BYTES = {"k_klt_batch": 432.44e6 + 0.90e6, "pyramid": 83.12e6 + 271.34e6}
 SM_MAX_MHZ = 2070.0
 
 
