@@ -19,8 +19,9 @@
 // of the integer footprint of J under the window (cell_moments).  A sweep
 // over the footprint is needed only when the integer part of q changes;
 // iterations that stay in the same cell reuse the moments.  The template and
-// its gradients stay in registers (3 * win floats per lane); the footprint is
-// staged in per-warp shared memory.  Sums over the window are per-lane FP32
+// its gradients stay in registers (3 * win floats per lane); the image and
+// gradient window it is sampled from, and each footprint, are staged in
+// per-warp shared memory by cp.async.  Sums over the window are per-lane FP32
 // sums over rows followed by a warp reduction that leaves bit-identical
 // totals in every lane (an XOR butterfly, or a reduce-scatter and broadcast),
 // so control flow stays warp-uniform.
@@ -151,8 +152,10 @@ __device__ __forceinline__ float kdiff(float a, float b, float c, float d) {
 // 2^-l exactly.
 __device__ __forceinline__ float pow2neg(int l) { return __int_as_float((127 - l) << 23); }
 
-// Per-warp shared scratch: the staged footprint of J for one window sweep
-// (win + 1 rows of NC 16-byte chunks).
+// Per-warp shared scratch: the staged (win + 1)^2 window of a level image --
+// the footprint of J for one sweep, or the template's source -- in win + 1
+// rows of NC 16-byte chunks, and the template's gradient window in win + 1
+// rows of NG 16-byte chunks.
 template <int WIN>
 struct KSmem {
     static constexpr int NC = (WIN + 31) / 16;  // 16-byte chunks per staged row: cover 15 + win + 1 bytes
@@ -160,6 +163,9 @@ struct KSmem {
     static_assert(JS >= 15 + WIN + 1 && JS - 1 - WIN <= 32, "a staged row covers the footprint row and reads "
                                                               "at most 32 bytes past it (the allocation keeps 256)");
     uint8_t j[(WIN + 1) * JS];
+    static constexpr int NG = (4 * (3 + WIN + 1) + 15) / 16;  // 16-byte chunks per staged gradient row
+    static constexpr int GS = NG * 4;                         // staged gradient row stride in words
+    uint32_t g[(WIN + 1) * GS];
 };
 
 // Template of a level without stored gradients: lane c computes the raw
@@ -246,31 +252,62 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
 }
 
 // Sample the template of level `L` around (ux, uy): lane c ends with column
-// c of T and of its gradients (zero for c >= WIN).
+// c of T and of its gradients (zero for c >= WIN).  The (win + 1)^2 image and
+// gradient footprint is first staged in shared memory (16-byte cp.async
+// chunks of each clamped row when the columns lie inside the level, else one
+// clamped column per lane).
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
-                                              float (&GX)[WIN], float (&GY)[WIN]) {
+                                              float (&GX)[WIN], float (&GY)[WIN], KSmem<WIN> &sm) {
     if constexpr (GT == VT_GRAD_NONE) {
         load_template_otf<WIN>(L, ux, uy, lane, T, GX, GY);
         return;
     }
     constexpr int HW = WIN / 2;
+    constexpr int NC = KSmem<WIN>::NC, JS = KSmem<WIN>::JS, NG = KSmem<WIN>::NG, GS = KSmem<WIN>::GS;
     const float fx = floorf(ux), fy = floorf(uy);
     const float ax = ux - fx, ay = uy - fy;
     const int x0 = (int)fx - HW, y0 = (int)fy - HW;
-    const int col = clampi(x0 + lane, 0, L.w - 1);
-    const uint8_t *ib = L.img + col;
-    const uint32_t *gb = L.grad + col;
-    const bool ld = lane <= WIN;
+    const int hm1 = L.h - 1;
+    int offi, offg;
+    __syncwarp();
+    if (x0 >= 0 && x0 + WIN < L.w) {
+        const int wx = x0 & ~15, gw = x0 & ~3;
+        offi = x0 - wx;
+        offg = x0 - gw;
+        const uint32_t sbj = (uint32_t)__cvta_generic_to_shared(sm.j);
+        const uint32_t sbg = (uint32_t)__cvta_generic_to_shared(sm.g);
+        for (int k = lane; k < (WIN + 1) * NC; k += 32) {
+            const int row = k / NC, c = k - row * NC;
+            const uint8_t *src = L.img + (size_t)clampi(y0 + row, 0, hm1) * L.pitch + wx + 16 * c;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbj + row * JS + 16 * c), "l"(src) : "memory");
+        }
+        for (int k = lane; k < (WIN + 1) * NG; k += 32) {
+            const int row = k / NG, c = k - row * NG;
+            const uint32_t *src = L.grad + (size_t)clampi(y0 + row, 0, hm1) * L.gpitch + gw + 4 * c;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbg + 4 * (row * GS + 4 * c)), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else {
+        offi = offg = 0;
+        if (lane <= WIN) {
+            const int c = clampi(x0 + lane, 0, L.w - 1);
+#pragma unroll
+            for (int r = 0; r <= WIN; ++r) {
+                const int row = clampi(y0 + r, 0, hm1);
+                sm.j[r * JS + lane] = __ldg(L.img + (size_t)row * L.pitch + c);
+                sm.g[r * GS + lane] = __ldg(L.grad + (size_t)row * L.gpitch + c);
+            }
+        }
+    }
+    __syncwarp();
+    const int cl = lane <= WIN ? lane : WIN;
+    const uint8_t *jr = &sm.j[offi + cl];
+    const uint32_t *gr = &sm.g[offg + cl];
     float pi = 0.f, pgx = 0.f, pgy = 0.f;
 #pragma unroll
     for (int r = 0; r <= WIN; ++r) {
-        const int row = clampi(y0 + r, 0, L.h - 1);
-        uint32_t v = 0, g = 0;
-        if (ld) {
-            v = __ldg(ib + (size_t)row * L.pitch);
-            g = __ldg(gb + (size_t)row * L.gpitch);
-        }
+        const uint32_t v = jr[r * JS], g = gr[r * GS];
         const float mv = u8f(v);
         const float mvr = __shfl_down_sync(kFull, mv, 1);
         float gx, gy;
@@ -447,7 +484,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         const Level Jl = J[l];
         const float s = pow2neg(l);
         const float ux = ux0 * s, uy = uy0 * s;
-        load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY);
+        load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY, sm);
         ++o.tmpl;
         float a11 = 0.f, a12 = 0.f, a22 = 0.f;
 #pragma unroll

@@ -212,3 +212,45 @@ def test_argument_errors():
     q = vt.vt_pyramid_build_grad(img, 3, vt.VT_GRAD_F16)
     with pytest.raises(vt.VTError):  # fused FB needs one gradient type
         vt.vt_klt_track_fb(p, q, e, vt.KltParams(levels=3), e, s)
+
+
+def test_near_singular_gradient_matrix_lambda_min():
+    """λ_min of a nearly rank-one G.  Diagonal stripes of contrast 8 with a
+    few pixels changed by one grey level keep every window sum of gradient
+    products below 2^24, so the GPU's FP32 sums are exact integers equal to
+    the oracle's: the only rounding left on the GPU is in λ_max (a square
+    root) and in the determinant g11 g22 - g12^2.  For these points the
+    determinant cancels by a factor ≥ 1e3 (a plain FP32 product difference
+    would be off by far more than the bound below), and λ_min must match the
+    oracle's exact one to 2e-6 relative."""
+    vt = _vt()
+    rng = np.random.default_rng(21)
+    h, w = 96, 128
+    y, x = np.mgrid[0:h, 0:w]
+    img = (100 + 8 * ((x + y) % 6 < 3)).astype(np.uint8)
+    flip = rng.random((h, w)) < 0.003
+    img[flip] ^= 1
+    pts = np.stack(np.meshgrid(np.arange(16, 112, 6), np.arange(16, 80, 6)), -1).reshape(-1, 2).astype(np.float32)
+    prm = vt.KltParams(win=21, levels=1, max_iters=5, eps=0.01, min_eig=0.0)
+    g = _gpu_track(img, img, pts, prm)
+    r = _ref(img, img, pts, prm)
+    # G from the oracle's integer gradients (raw Scharr) at the integer points
+    rp = oracle.build_pyramid(img, 1)
+    gx, gy = rp.gx[0].astype(np.int64), rp.gy[0].astype(np.int64)
+    cancel, naive_err = [], []
+    for px, py in pts.astype(int):
+        wx = gx[py - 10:py + 11, px - 10:px + 11]
+        wy = gy[py - 10:py + 11, px - 10:px + 11]
+        a, b, c = int((wx * wx).sum()), int((wx * wy).sum()), int((wy * wy).sum())
+        assert max(a, b, c) < 2 ** 24  # exact FP32 sums
+        det = a * c - b * b
+        naive = float(np.float32(np.float32(a) * np.float32(c)) - np.float32(np.float32(b) * np.float32(b)))
+        cancel.append(a * c / det if det > 0 else np.inf)
+        naive_err.append(abs(naive - det) / det if det > 0 else np.inf)
+    cancel, naive_err = np.array(cancel), np.array(naive_err)
+    sel = (r.status == 1) & (g["status"] == 1) & (cancel >= 1e3) & np.isfinite(cancel)
+    assert sel.sum() >= 10, (sel.sum(), np.sort(cancel)[:10])
+    # the bound below separates a compensated determinant from a plain one
+    assert np.median(naive_err[sel]) > 1e-5
+    np.testing.assert_allclose(g["lmin"][sel], r.lmin[sel], rtol=2e-6)
+    assert (g["status"] == r.status).all()
