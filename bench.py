@@ -39,7 +39,7 @@ SM_COUNT = 152
 # dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before each
 # captured launch, mean of two captured steps), summarised in
 # profiles/launches_bench_32streams.md.  Reported only for that workload.
-NCU_TRAFFIC_BYTES = {"k_klt_batch": 432.44e6 + 0.90e6, "pyramid": 83.12e6 + 271.34e6}
+NCU_TRAFFIC_BYTES = {"k_klt_batch": 439.43e6 + 1.24e6, "pyramid": 83.19e6 + 271.38e6}
 SM_MAX_MHZ = 2070.0
 
 
