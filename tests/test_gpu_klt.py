@@ -254,3 +254,31 @@ def test_near_singular_gradient_matrix_lambda_min():
     assert np.median(naive_err[sel]) > 1e-5
     np.testing.assert_allclose(g["lmin"][sel], r.lmin[sel], rtol=2e-6)
     assert (g["status"] == r.status).all()
+
+
+@pytest.mark.parametrize("win", [9, 15, 21, 31])
+def test_borders_and_tiny_levels_against_oracle(win):
+    """Windows that cross every image edge, on a small smooth image with five
+    levels (down to 4 x 3 px) and on a wider one with a window-wide margin:
+    the staged template and footprint windows take their clamped-row chunk
+    path, their one-column-per-lane path and (levels narrower than the
+    window) only the latter.  Forward-backward tracking against the oracle
+    under the usual flow and margin rules."""
+    from scipy.ndimage import gaussian_filter
+
+    vt = _vt()
+    rng = np.random.Generator(np.random.PCG64(100 + win))
+    for w, h in ((53, 37), (160, 96)):
+        base = gaussian_filter(rng.uniform(0, 255, (h + 8, w + 8)), 1.5)
+        I = np.clip(base[4:4 + h, 4:4 + w] * 1.6 - 70, 0, 255).astype(np.uint8)
+        J = np.clip(base[3:3 + h, 6:6 + w] * 1.6 - 70, 0, 255).astype(np.uint8)  # (+2, +1) px shift
+        xs = np.concatenate([[0, 0.5, 1.25, 3.0, w - 4.5, w - 2.0, w - 1.25, w - 1], rng.uniform(0, w - 1, 40)])
+        ys = np.concatenate([[0, h - 1, 0.75, h - 2.5, 2.0, 3.5, h - 3.25, 0], rng.uniform(0, h - 1, 40)])
+        pts = np.stack([xs, ys], 1).astype(np.float32)
+        for levels in (1, 3, 5):
+            prm = vt.KltParams(win=win, levels=levels, min_eig=1e-5)
+            g = _gpu_track(I, J, pts, prm, fb=True)
+            r = _ref(I, J, pts, prm, fb=True)
+            st = _check(g, r, f"{w}x{h} win {win} L{levels}", fb=True)
+            if levels < 5:  # at five levels the top is a few pixels wide: most points fail the eigenvalue test
+                assert st["tracked_ref"] >= 30, st
