@@ -165,6 +165,8 @@ struct KSmem {
     uint8_t j[(WIN + 1) * JS];
     static constexpr int NG = (4 * (3 + WIN + 1) + 15) / 16;  // 16-byte chunks per staged gradient row
     static constexpr int GS = NG * 4;                         // staged gradient row stride in words
+    static_assert(GS >= 3 + WIN + 1 && 4 * (GS - WIN - 1) <= 32, "a staged gradient row covers the window row "
+                                                                 "and reads at most 32 bytes past it");
     uint32_t g[(WIN + 1) * GS];
 };
 
@@ -254,7 +256,9 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
 // Sample the template of level `L` around (ux, uy): lane c ends with column
 // c of T and of its gradients (zero for c >= WIN).  The (win + 1)^2 image and
 // gradient footprint is first staged in shared memory (16-byte cp.async
-// chunks of each clamped row when the columns lie inside the level, else one
+// chunks of each clamped row when the columns lie inside the level -- they
+// may read up to 26 image bytes and 24 gradient bytes past a row's last
+// pixel, inside the pitch or the pyramid allocation's slack -- else one
 // clamped column per lane).
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
