@@ -662,8 +662,7 @@ def run_native(a, rank, world, local_rank):
         "data": "synthetic",
         "impl": "native",
         "config": {
-            "workload": f"batched: {S} camera streams (640x480..1920x1200, mono/stereo, 200-2000 keypoints, "
-                        f"4-6 levels), one new frame per stream per step, FB-checked temporal + stereo tracking",
+            "workload": workload_name(S),
             "streams": S,
             "stereo_streams": sum(1 for s in specs if s.stereo),
             "features_per_step": feats // a.steps,
@@ -829,31 +828,48 @@ def cpu_model() -> str:
     return f"{name or 'unknown'} ({os.cpu_count()} cores)"
 
 
+def workload_name(n_streams):
+    return (f"batched: {n_streams} camera streams (640x480..1920x1200, mono/stereo, 200-2000 keypoints, "
+            f"4-6 levels), one new frame per stream per step, FB-checked temporal + stereo tracking")
+
+
 def cpu_baseline(specs, frames, prm, seconds):
     """The FP64 oracle, single-threaded, on a bounded sample of step 1 of the
     same workload: pyramids + Scharr of the frames it needs, then the
-    FB-checked tracking of each stream's points, stream after stream, until
-    `seconds` have passed."""
+    FB-checked tracking of each stream's points with the stream's own level
+    count (as the batched run does), stream after stream, until `seconds`
+    have passed.  Also reports the oracle's Newton iterations per pyramid
+    level, the it_l of the algorithmic FLOP count."""
     import oracle
 
     t0 = time.perf_counter()
     feats = 0
     streams = 0
-    pts_done = 0
+    it_sum = [0] * 8
+    it_n = [0] * 8
+
+    def count(res, L):
+        for rr in (res.fwd, res.bwd):
+            tot = rr.iters_level.sum(axis=0)
+            for lv in range(L):
+                it_sum[lv] += int(tot[lv])
+                it_n[lv] += rr.iters_level.shape[0]
+
     for sp, fr in zip(specs, frames):
-        L = prm.levels
-        p0 = oracle.build_pyramid(fr.left[0], sp.levels)
-        p1 = oracle.build_pyramid(fr.left[1], sp.levels)
+        L = sp.levels
+        p0 = oracle.build_pyramid(fr.left[0], L)
+        p1 = oracle.build_pyramid(fr.left[1], L)
         chunk = 64
         kp = fr.kps[0]
         for c in range(0, len(kp), chunk):
-            oracle.track_fb(p0, p1, kp[c:c + chunk], prm.win, L, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
-            pts_done += len(kp[c:c + chunk])
+            count(oracle.track_fb(p0, p1, kp[c:c + chunk], prm.win, L, prm.max_iters, prm.eps, prm.min_eig,
+                                  prm.fb_thr, per_level=True), L)
             if sp.stereo:
                 if c == 0:
-                    pr = oracle.build_pyramid(fr.right[1], sp.levels)
+                    pr = oracle.build_pyramid(fr.right[1], L)
                 kq = fr.kps[1][c:c + chunk]
-                oracle.track_fb(p1, pr, kq, prm.win, L, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
+                count(oracle.track_fb(p1, pr, kq, prm.win, L, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr,
+                                      per_level=True), L)
             feats += len(kp[c:c + chunk])
             if time.perf_counter() - t0 > seconds:
                 break
@@ -863,7 +879,11 @@ def cpu_baseline(specs, frames, prm, seconds):
     dt = time.perf_counter() - t0
     return {"value": feats / dt, "unit": "features/s", "cores": 1, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"step 1 of the same workload: {feats} features of {streams} stream(s) incl. their pyramids, "
-                      f"FP64 single-threaded C, {dt:.1f} s"}
+                      f"FP64 single-threaded C, {dt:.1f} s",
+            "iters_per_level": {f"L{lv}": round(it_sum[lv] / it_n[lv], 3) for lv in range(8) if it_n[lv]},
+            "iters_note": "the oracle's mean Newton iterations at each level (L0 = finest) per point and pass "
+                          "(forward and backward, temporal and stereo) in this sample; the tracking kernel's "
+                          "per-point totals equal the oracle's wherever no convergence decision is marginal"}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -875,8 +895,8 @@ def run_reference(a, rank, world):
         return None
     import oracle
 
+    # the first streams of the same seeded mix (the mix draws stream after stream)
     specs, frames = make_workload(min(a.streams, 8), a.frames, a.seed, os.cpu_count() or 1)
-    prm_levels = min(sp.levels for sp in specs)
     F = a.frames
 
     def one(t):
@@ -885,10 +905,10 @@ def run_reference(a, rank, world):
         p0 = oracle.build_pyramid(fr.left[fp], sp.levels)
         p1 = oracle.build_pyramid(fr.left[fc], sp.levels)
         kp = fr.kps[fp][:128]
-        oracle.track_fb(p0, p1, kp, 21, prm_levels, 30, 0.01, 1e-4, 0.5)
+        oracle.track_fb(p0, p1, kp, 21, sp.levels, 30, 0.01, 1e-4, 0.5)
         if sp.stereo:
             pr = oracle.build_pyramid(fr.right[fc], sp.levels)
-            oracle.track_fb(p1, pr, fr.kps[fc][:128], 21, prm_levels, 30, 0.01, 1e-4, 0.5)
+            oracle.track_fb(p1, pr, fr.kps[fc][:128], 21, sp.levels, 30, 0.01, 1e-4, 0.5)
         return len(kp)
 
     for i in range(a.warmup):
@@ -907,8 +927,9 @@ def run_reference(a, rank, world):
         "metric": METRIC, "value": v, "unit": "features/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "batched stream mix, bounded sample per step: 128 keypoints of one stream "
-                               "(temporal + stereo FB tracking, pyramids included)", "streams": len(specs)},
+        "config": {"workload": workload_name(a.streams), "streams": a.streams,
+                   "sample": f"per step 128 keypoints of one of the first {len(specs)} streams, cycling (temporal "
+                             "+ stereo FB tracking with the stream's levels, pyramids included)", "seed": a.seed},
         "latency_ms": {"p50": times[len(times) // 2] * 1e3, "p99": times[min(len(times) - 1,
                                                                               int(0.99 * len(times)))] * 1e3},
         "cpu_baseline": {"value": v, "unit": "features/s", "cores": 1, "cpu": cpu_model(), "kind": "oracle",

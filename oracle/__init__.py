@@ -34,7 +34,7 @@ def _load():
         lib.orc_pyrdown.argtypes = [u8p, C.c_int, C.c_int, C.c_int, u8p, C.c_int]
         lib.orc_scharr.argtypes = [u8p, C.c_int, C.c_int, C.c_int, i16p, i16p, C.c_int]
         lib.orc_track.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, f64p, C.c_void_p, C.c_int,
-                                  f64p, u8p, f64p, u8p, i32p, f64p, f64p]
+                                  f64p, u8p, f64p, u8p, i32p, f64p, f64p, C.c_void_p]
         lib.orc_fb_check.argtypes = [f64p, f64p, u8p, u8p, C.c_int, C.c_double, u8p, f64p, f64p]
         f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
         lib.orc_gftt.restype = C.c_int
@@ -104,6 +104,7 @@ class TrackResult:
     iters: np.ndarray  # int32 [n]
     lmin: np.ndarray  # float64 [n]
     margin: np.ndarray  # float64 [n, 3]: eig (relative), conv (px), bound (px)
+    iters_level: np.ndarray | None = None  # int32 [n, levels]: Newton iterations per level (on request)
 
 
 def _levels_struct(levels_f64):
@@ -124,7 +125,7 @@ def _levels_struct(levels_f64):
 
 
 def track_f64(levels_I, levels_J, pts, win=21, levels=None, max_iters=30, eps=0.01, min_eig=1e-4,
-              guess=None) -> TrackResult:
+              guess=None, per_level=False) -> TrackResult:
     """Core LK on double-valued levels.  ``levels_I``: list of (img, gx, gy)
     with gradients in grey levels per pixel; ``levels_J``: list of images."""
     L = len(levels_I) if levels is None else levels
@@ -147,19 +148,21 @@ def track_f64(levels_I, levels_J, pts, win=21, levels=None, max_iters=30, eps=0.
     it = np.zeros(n, np.int32)
     lm = np.zeros(n)
     mg = np.zeros((n, 3))
+    il = np.zeros((n, L), np.int32) if per_level else None
     _load().orc_track(C.addressof(Is), C.addressof(Js), C.addressof(prm), pts,
-                      None if g is None else g.ctypes.data, n, out, st, err, rs, it, lm, mg)
-    return TrackResult(out, st, err, rs, it, lm, mg)
+                      None if g is None else g.ctypes.data, n, out, st, err, rs, it, lm, mg,
+                      None if il is None else il.ctypes.data)
+    return TrackResult(out, st, err, rs, it, lm, mg, il)
 
 
 def track(pI: Pyramid, pJ: Pyramid, pts, win=21, levels=None, max_iters=30, eps=0.01, min_eig=1e-4,
-          guess=None) -> TrackResult:
+          guess=None, per_level=False) -> TrackResult:
     """LK from pyramid ``pI`` to ``pJ`` on uint8 levels and raw int16 Scharr
     gradients (converted to grey levels per pixel by the factor 1/32)."""
     L = len(pI.levels) if levels is None else levels
     lvI = [(pI.levels[k].astype(np.float64), pI.gx[k] / 32.0, pI.gy[k] / 32.0) for k in range(L)]
     lvJ = [pJ.levels[k].astype(np.float64) for k in range(L)]
-    return track_f64(lvI, lvJ, pts, win, L, max_iters, eps, min_eig, guess)
+    return track_f64(lvI, lvJ, pts, win, L, max_iters, eps, min_eig, guess, per_level)
 
 
 def fb_check(p0, p0_back, st_f, st_b, thr=0.5):
@@ -191,13 +194,13 @@ class FBResult:
 
 
 def track_fb(pI: Pyramid, pJ: Pyramid, pts, win=21, levels=None, max_iters=30, eps=0.01, min_eig=1e-4,
-             fb_thr=0.5) -> FBResult:
+             fb_thr=0.5, per_level=False) -> FBResult:
     """Forward I->J from ``pts``, backward J->I from the forward result, FB test.
 
     The stereo gate of Sec. V-A (only features passing the cross-camera
     optical-flow check enter the pool) is this call with (I, J) = (left, right)."""
-    f = track(pI, pJ, pts, win, levels, max_iters, eps, min_eig)
-    b = track(pJ, pI, f.pts, win, levels, max_iters, eps, min_eig)
+    f = track(pI, pJ, pts, win, levels, max_iters, eps, min_eig, per_level=per_level)
+    b = track(pJ, pI, f.pts, win, levels, max_iters, eps, min_eig, per_level=per_level)
     st, d, m = fb_check(pts, b.pts, f.status, b.status, fb_thr)
     reason = f.reason.copy()
     reason[(reason == 0)] = b.reason[(reason == 0)]

@@ -141,13 +141,14 @@ static double dmin(double a, double b) { return a < b ? a : b; }
  *   err     [n]    mean |T - J| at level 0 (0 when lost)
  *   reason  [n]    ORC_* code
  *   iters   [n]    Newton iterations summed over levels
+ *   iters_level [n][levels] (may be NULL) Newton iterations at each level
  *   lmin    [n]    normalised lambda_min of G at the last level examined
  *   margin  [n][3] smallest |lambda_min - min_eig| / min_eig, |  |eta| - eps |,
  *                  and distance to the image-bound tests
  */
 void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, const double *pts,
                const double *guess, int n, double *out, uint8_t *status, double *err, uint8_t *reason,
-               int32_t *iters, double *lmin, double *margin)
+               int32_t *iters, double *lmin, double *margin, int32_t *iters_level)
 {
     const int win = prm->win, hw = win / 2, N = win * win, L = prm->levels;
     double *T = (double *)malloc(sizeof(double) * 3 * (size_t)N);
@@ -159,6 +160,8 @@ void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, co
         double gx = 0.0, gy = 0.0, nux = 0.0, nuy = 0.0;
         double ex = 0.0, ey = 0.0;
         int lost_level = -1;
+        if (iters_level)
+            for (int l = 0; l < L; ++l) iters_level[(size_t)p * L + l] = 0;
         if (!(ux0 >= 0.0 && ux0 <= I[0].w - 1 && uy0 >= 0.0 && uy0 <= I[0].h - 1)) {
             st = 0;
             rs = ORC_LOST_INPUT;
@@ -221,6 +224,7 @@ void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, co
                 nux += ex;
                 nuy += ey;
                 ++it;
+                if (iters_level) ++iters_level[(size_t)p * L + l];
                 m_conv = dmin(m_conv, fabs(sqrt(ex * ex + ey * ey) - prm->eps));
                 if (ex * ex + ey * ey < prm->eps * prm->eps) break;
             }

@@ -162,10 +162,12 @@ def test_level_propagation_iteration_count_on_bowl():
     propagation (or level scaling) costs a second pass somewhere."""
     t = (12.0, -8.0)
     lvI, lvJ = _bowl_levels(t, 3)
-    r = oracle.track_f64(lvI, lvJ, np.array([[128.0, 128.0]]), win=21, max_iters=10, eps=1e-9, min_eig=1e-12)
+    r = oracle.track_f64(lvI, lvJ, np.array([[128.0, 128.0]]), win=21, max_iters=10, eps=1e-9, min_eig=1e-12,
+                         per_level=True)
     assert r.status[0] == 1
     np.testing.assert_allclose(r.pts[0], [140.0, 120.0], atol=1e-9)
     assert r.iters[0] == 2 + 1 + 1
+    assert r.iters_level[0].tolist() == [1, 1, 2]  # levels 0, 1, 2: the top one does the work
 
 
 def test_convergence_test_is_on_the_step_length():
@@ -198,10 +200,11 @@ def test_min_eigenvalue_closed_form_quadratic():
 def test_zero_motion_is_exact():
     c = synth.make_config1(1)
     p = oracle.build_pyramid(c.I, 4)
-    r = oracle.track(p, p, c.pts)
+    r = oracle.track(p, p, c.pts, per_level=True)
     assert np.all(r.status == 1)
     assert np.array_equal(r.pts, c.pts.astype(np.float64))
     assert np.all(r.iters == 4)  # one pass per level with eta = 0
+    assert np.all(r.iters_level == 1)
     assert np.all(r.err == 0.0)
 
 
