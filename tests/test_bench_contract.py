@@ -46,3 +46,20 @@ def test_native_small_run_line():
     for sec in ("gftt", "stereo_gate", "track_bookkeeping", "frontend_loop", "plain"):
         assert d[sec], sec
     assert d["config"]["launch_shape"]["warps_per_cta"] in (4, 8)
+
+
+def test_cpu_baseline_uses_stream_levels_and_counts_iterations():
+    """The native arm's CPU baseline: the oracle on a bounded sample, each
+    stream with its own level count, and the mean Newton iterations per
+    level of that sample."""
+    from types import SimpleNamespace
+
+    import bench
+
+    specs, frames = bench.make_workload(1, 2, 4, 1)
+    prm = SimpleNamespace(win=21, levels=4, max_iters=30, eps=0.01, min_eig=1e-4, fb_thr=0.5)
+    r = bench.cpu_baseline(specs, frames, prm, 0.5)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] == 1
+    il = r["iters_per_level"]
+    assert sorted(il) == [f"L{lv}" for lv in range(specs[0].levels)]
+    assert all(v > 0 for v in il.values())
