@@ -78,9 +78,10 @@ def test_precision_workload_1280x1024_int16(precision_seq):
 def test_precision_workload_fp16_gradients_error_stated(precision_seq):
     """FP16 gradient storage changes the weights of b = sum r grad T and the
     eigenvalue test by the half-precision rounding of raw/32 (relative
-    2^-11), so its flow differs from the FP64 oracle on int16 gradients by a
-    small amount and a few eigenvalue decisions near the threshold flip.
-    Measured and bounded here; the exact numbers are in the project notes."""
+    2^-11) wherever an odd Scharr response exceeds 2048 (smaller or even
+    responses are exact in half precision), so its flow may differ from the
+    FP64 oracle on int16 gradients by a small amount and a few eigenvalue
+    decisions near the threshold may flip.  Measured and bounded here."""
     import paper_2607_01757_gb300 as vt
 
     seq = precision_seq
