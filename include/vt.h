@@ -160,8 +160,9 @@ VT_API void vt_pyramid_free(vt_pyramid *p);
  * Outputs (device, caller-owned, n entries): pts_out = v (for a lost point:
  * its last estimate, scaled to level 0), status = 1 tracked / 0 lost,
  * err = mean |T(x) - J_0(v + x)| over the window (0 when lost; nullable).
- * G, b and the residual are accumulated in FP32; the 2x2 solve falls back to
- * FP64 when lambda_max / lambda_min > 1e5.
+ * G, b and the residual are accumulated in FP32; det(G) and the adjugate
+ * products of the 2x2 solve are evaluated in FP32 with Kahan's FMA scheme
+ * (relative error <= 2 ulp, sign exact), so no FP64 is used.
  * win: one of VT_SUPPORTED_WINDOWS.  levels: 1..min(prev, cur levels).
  * max_iters >= 1, eps >= 0.  n == 0 launches nothing.
  */
