@@ -493,35 +493,59 @@ VT_API vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream);
 VT_API vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void *ev_pyr1, void *ev_klt0,
                                     void *ev_klt1);
 
+/* vt_batch_run_timed that also records one event after each pyramid launch:
+ * events[0..3] as ev_pyr0, ev_pyr1, ev_klt0, ev_klt1 of vt_batch_run_timed,
+ * events[4 + i] after pyramid launch i (the tiled launches of levels 0, 1,
+ * .., then the tail launch).  `nevents` must be at least 4 + the staged
+ * run's pyramid launches (launches_per_run of vt_batch_info minus the
+ * tracking and gate launches); VT_ERR_ARG otherwise.  Null entries are
+ * skipped. */
+VT_API vt_status vt_batch_run_levels_timed(vt_batch *b, void *cuda_stream, void **events, int nevents);
+
 /* Launch shape of the staged run and the number of kernel launches per run. */
 VT_API vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
                                int *launches_per_run);
 
 /*
  * vt_klt_track_tasks_noalloc - the batched tracking launch for callers that
- * cannot allocate device memory when they call: code running while a stream
- * is captured into a CUDA graph (cudaMalloc cannot be captured), real-time
- * loops that must not wait on the allocator or on the device-wide
- * synchronisation cudaFree may cause, and hosts that own all device memory.
+ * cannot allocate device memory when they call: real-time loops that must
+ * not wait on the allocator or on the device-wide synchronisation cudaFree
+ * may cause, and hosts (frameworks, plug-in hosts) that hand out all device
+ * memory from their own pools and forbid allocation by the code they call.
  * The paper has no counterpart; it is an addition of this library.
  *
  * Tracks `ntasks` tasks (vt_track_task, pyramids already built, one gradient
  * type, `prm` as for vt_batch_set) in one persistent launch, like the
  * tracking launch of vt_batch_run, with the same results.  Nothing is
  * allocated: the job table and the work counter live in a fixed array of
- * about 22 KB in device memory that every device loading the library keeps
- * until the process exits; the table is built on the host stack and copied
- * with one cudaMemcpyAsync.  Limit: at most 256 tasks per call (VT_ERR_ARG
- * beyond; any number of points per task up to 2^31 in total).
+ * 24,064 bytes in device memory that every device loading the library keeps
+ * until the process exits.  The table is handed to a small fill kernel as
+ * its launch parameter (a snapshot taken by the launch; no host buffer has
+ * to outlive the call), which writes it into the array and zeroes the
+ * counter; the tracking launch follows on the same stream.  Limit: at most
+ * 256 tasks per call (VT_ERR_ARG beyond; any number of points per task up
+ * to 2^31 in total).
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the array and overwrites it (the counter is reset by
- * each call's copy), so calls that overlap on the GPU - on different streams
+ * (cudaGetSymbolAddress) and keeps it.  Every call shares the array and
+ * overwrites it, so calls that overlap on the GPU - on different streams
  * without ordering, or from different threads - race; serialise them.
  */
 VT_API vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int ntasks, const vt_klt_params *prm,
                                             void *cuda_stream);
+
+/*
+ * vt_fp32_fma_probe - measurement helper, not part of the method: one launch
+ * of (SMs x 8) CTAs of 256 threads, each thread running 8 independent FP32
+ * FMA chains of 8 x `iters` FMAs, on `cuda_stream`.  Timing it with CUDA
+ * events gives this device's FP32 FMA throughput at its current clocks, the
+ * denominator of the tracking kernel's roofline.  `out`: device float array
+ * of at least SMs x 2048 entries (`out_floats` entries), overwritten with one
+ * value per thread; `*flops` (host) receives the launch's FLOP count
+ * (2 per FMA).  VT_ERR_ARG for iters < 1, null pointers or a short array.
+ */
+VT_API vt_status vt_fp32_fma_probe(int iters, float *out, long long out_floats, long long *flops,
+                                   void *cuda_stream);
 
 /* Human-readable name of a status code. */
 VT_API const char *vt_status_str(vt_status s);

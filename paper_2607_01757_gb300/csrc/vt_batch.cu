@@ -14,6 +14,7 @@
 // graph per topology (deepest pyramid, gradient type, window) replays any
 // batch: the host only rewrites the pinned tables between replays.  Two
 // staging buffers let the host prepare run t+1 while run t executes.
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -166,7 +167,9 @@ static int klt_grid(const vt_batch *b, int win, int gtype) {
     return b->sms * per;
 }
 
-static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+// ev (nullable): 4 events around the pyramid and tracking launches; lev
+// (nullable): one event after each pyramid launch.
+static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = nullptr, cudaEvent_t *lev = nullptr) {
     const Topo &tp = b->topo[k];
     if (cudaMemcpyAsync(b->dev[k], b->host[k], b->tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(b->counter + k, 0, sizeof(int), s) != cudaSuccess) {
@@ -174,7 +177,7 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
         return VT_ERR_CUDA;
     }
     if (ev && ev[0]) cudaEventRecord(ev[0], s);
-    vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, b->tail_grid, s);
+    vt_status st = launch_pyr_batch(b->dev[k], tp.maxL, tp.gtype, tp.pyr_grid, b->tail_grid, s, lev);
     if (st != VT_OK) return st;
     if (ev && ev[1]) cudaEventRecord(ev[1], s);
     const KltBatchKernel kb = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
@@ -454,6 +457,25 @@ vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr0, void
     return VT_OK;
 }
 
+vt_status vt_batch_run_levels_timed(vt_batch *b, void *cuda_stream, void **events, int nevents) {
+    if (!b || b->staged < 0 || !events || nevents < 0) return VT_ERR_ARG;
+    const int k = b->staged;
+    const int need = b->topo[k].maxL + 1 + 4;
+    if (nevents < need) return VT_ERR_ARG;
+    b->fresh = false;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t ev[4] = {(cudaEvent_t)events[0], (cudaEvent_t)events[1], (cudaEvent_t)events[2],
+                         (cudaEvent_t)events[3]};
+    vt_status st = enqueue(b, k, s, ev, reinterpret_cast<cudaEvent_t *>(events + 4));
+    if (st != VT_OK) return st;
+    if (cudaEventRecord(b->ev[k], s) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    b->ev_used[k] = true;
+    return VT_OK;
+}
+
 vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
     if (!b || b->staged < 0) return VT_ERR_ARG;
     const int k = b->staged;
@@ -509,13 +531,14 @@ vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_pe
 // ---------------------------------------------------------------------------
 // Tracking of many tasks without any allocation.
 //
-// Some callers cannot allocate device memory at call time: code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not a
-// capturable operation), real-time loops that must not block on the
-// allocator or on the implicit device synchronisation cudaFree can cause,
-// and hosts that hand out all device memory themselves.  For them the tracking
-// launch of vt_batch can run with its job table and work counter in the
-// file-scope array below instead of a vt_batch's allocations.
+// Some callers cannot allocate device memory at call time: real-time loops
+// that must not block on the allocator or on the device-wide synchronisation
+// cudaFree can cause, and hosts (frameworks, plug-in hosts) that hand out all
+// device memory from their own pools.  For them the tracking launch of
+// vt_batch can run with its job table and work counter in the file-scope
+// array below instead of a vt_batch's allocations.  The table travels to the
+// device as a kernel parameter (a snapshot taken at the launch), so no host
+// buffer has to outlive the call.
 namespace vt {
 
 constexpr int kNoAllocMaxTasks = 256;
@@ -524,30 +547,60 @@ constexpr size_t kNoAllocPrefixOff = kNoAllocTaskOff + sizeof(BTask) * kNoAllocM
 constexpr size_t kNoAllocCounterOff = (kNoAllocPrefixOff + sizeof(int) * kNoAllocMaxTasks + 255) / 256 * 256;
 constexpr size_t kNoAllocBytes = kNoAllocCounterOff + 256;
 static_assert(sizeof(BatchHdr) <= kNoAllocTaskOff, "header must fit before the task table");
+static_assert(kNoAllocBytes == 24064, "the size vt.h states");
 
 // Shared by every call on a device; kept until the process exits.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-static uint8_t *g_noalloc_ptr[kNoAllocMaxDevices];
+// The job table of one call, passed by value to k_noalloc_fill.
+struct NoAllocTable {
+    BatchHdr hdr;
+    BTask tasks[kNoAllocMaxTasks];
+    int prefix[kNoAllocMaxTasks];
+};
+static_assert(sizeof(NoAllocTable) <= 32000, "the table must fit the kernel-parameter limit");
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device; the array's host-side name is not an address).
+// Writes the header, the first `ntasks` tasks and prefix entries into the
+// scratch array and zeroes the work counter.  One CTA.
+__global__ void k_noalloc_fill(const __grid_constant__ NoAllocTable T) {
+    uint8_t *base = g_noalloc_scratch;
+    const int nt = T.hdr.ntasks;
+    const uint32_t *hs = reinterpret_cast<const uint32_t *>(&T.hdr);
+    uint32_t *hd = reinterpret_cast<uint32_t *>(base);
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchHdr) / 4); i += blockDim.x) hd[i] = hs[i];
+    const uint32_t *ts = reinterpret_cast<const uint32_t *>(T.tasks);
+    uint32_t *td = reinterpret_cast<uint32_t *>(base + kNoAllocTaskOff);
+    const int tw = nt * (int)(sizeof(BTask) / 4);
+    for (int i = threadIdx.x; i < tw; i += blockDim.x) td[i] = ts[i];
+    int *pd = reinterpret_cast<int *>(base + kNoAllocPrefixOff);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) pd[i] = T.prefix[i];
+    if (threadIdx.x == 0) *reinterpret_cast<int *>(base + kNoAllocCounterOff) = 0;
+}
+static_assert(sizeof(BatchHdr) % 4 == 0 && sizeof(BTask) % 4 == 0, "word copies");
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::atomic<uint8_t *> g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device, looked up on
+// the first call per device (the array's host-side name is not an address).
+// Threads racing on a first call look it up twice and store the same value.
 static vt_status noalloc_scratch(uint8_t **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
         cudaGetLastError();
         return VT_ERR_CUDA;
     }
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    uint8_t *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) {
             cudaGetLastError();
             return VT_ERR_CUDA;
         }
-        g_noalloc_ptr[dev] = (uint8_t *)p;
+        p = (uint8_t *)q;
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return VT_OK;
 }
 
@@ -575,14 +628,15 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
     }
     if (total > 0x7fffffff) return VT_ERR_ARG;
     if (total == 0) return VT_OK;
+    const KltBatchKernel kb = klt_batch_kernel(prm->win, gtype, 4);
+    if (!kb.fn) return VT_ERR_ARG;
     uint8_t *dev = nullptr;
     vt_status st = noalloc_scratch(&dev);
     if (st != VT_OK) return st;
-    // job table built on the host stack, copied into the scratch array with
-    // the work counter zeroed in the same copy
-    alignas(16) uint8_t host[kNoAllocCounterOff + sizeof(int)];
-    memset(host, 0, sizeof(host));
-    BatchHdr *H = reinterpret_cast<BatchHdr *>(host);
+    // the job table, built here and handed to the fill kernel by value
+    static thread_local NoAllocTable T;
+    memset(&T.hdr, 0, sizeof(T.hdr));
+    BatchHdr *H = &T.hdr;
     H->ntasks = ntasks;
     H->total_points = (int)total;
     H->off_tasks = (int)kNoAllocTaskOff;
@@ -593,34 +647,28 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
     H->P.eps2 = prm->eps * prm->eps;
     H->P.min_eig = prm->min_eig;
     H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
-    BTask *bt = reinterpret_cast<BTask *>(host + kNoAllocTaskOff);
-    int *p0s = reinterpret_cast<int *>(host + kNoAllocPrefixOff);
     int p0 = 0;
     for (int t = 0; t < ntasks; ++t) {
         const vt_track_task &tk = tasks[t];
-        bt[t].I = tk.prev->dev_lv;
-        bt[t].J = tk.cur->dev_lv;
-        bt[t].pts_in = reinterpret_cast<const float2 *>(tk.pts_in);
-        bt[t].pts_out = reinterpret_cast<float2 *>(tk.pts_out);
-        bt[t].status = tk.status;
-        bt[t].err = tk.err;
-        bt[t].reason = tk.reason;
-        bt[t].flops = tk.flops;
-        bt[t].n_dev = tk.n_dev;
-        bt[t].n = tk.n;
-        bt[t].fb = tk.fb ? 1 : 0;
-        bt[t].levels = tk.levels > 0 ? tk.levels : prm->levels;
-        bt[t].p0 = p0;
-        p0s[t] = p0;
+        BTask &b = T.tasks[t];
+        b.I = tk.prev->dev_lv;
+        b.J = tk.cur->dev_lv;
+        b.pts_in = reinterpret_cast<const float2 *>(tk.pts_in);
+        b.pts_out = reinterpret_cast<float2 *>(tk.pts_out);
+        b.status = tk.status;
+        b.err = tk.err;
+        b.reason = tk.reason;
+        b.flops = tk.flops;
+        b.n_dev = tk.n_dev;
+        b.n = tk.n;
+        b.fb = tk.fb ? 1 : 0;
+        b.levels = tk.levels > 0 ? tk.levels : prm->levels;
+        b.p0 = p0;
+        T.prefix[t] = p0;
         p0 += tk.n;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (cudaMemcpyAsync(dev, host, sizeof(host), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return VT_ERR_CUDA;
-    }
-    const KltBatchKernel kb = klt_batch_kernel(prm->win, gtype, 4);
-    if (!kb.fn) return VT_ERR_ARG;
+    k_noalloc_fill<<<1, 256, 0, s>>>(T);
     int sms = 0, occ = 0, d = 0;
     cudaGetDevice(&d);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
