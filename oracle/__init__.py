@@ -103,8 +103,19 @@ class TrackResult:
     reason: np.ndarray  # uint8 [n]
     iters: np.ndarray  # int32 [n]
     lmin: np.ndarray  # float64 [n]
-    margin: np.ndarray  # float64 [n, 3]: eig (relative), conv (px), bound (px)
+    margin: np.ndarray  # float64 [n, 4]: eig (relative), conv at every iteration (px), bound (px),
+    #                     conv at the iterations that stopped a level (px)
     iters_level: np.ndarray | None = None  # int32 [n, levels]: Newton iterations per level (on request)
+
+    def decision_margin(self, reason: int) -> np.ndarray:
+        """Per point, the smallest margin of the status decisions of one kind
+        (a LOST_* code): the eigenvalue test (relative) or the image-bound test
+        (px); other kinds are not decided by a single pass (infinite)."""
+        if reason == LOST_EIG:
+            return self.margin[:, 0]
+        if reason == LOST_OOB:
+            return self.margin[:, 2]
+        return np.full(self.margin.shape[0], np.inf)
 
 
 def _levels_struct(levels_f64):
@@ -147,7 +158,7 @@ def track_f64(levels_I, levels_J, pts, win=21, levels=None, max_iters=30, eps=0.
     rs = np.zeros(n, np.uint8)
     it = np.zeros(n, np.int32)
     lm = np.zeros(n)
-    mg = np.zeros((n, 3))
+    mg = np.zeros((n, 4))
     il = np.zeros((n, L), np.int32) if per_level else None
     _load().orc_track(C.addressof(Is), C.addressof(Js), C.addressof(prm), pts,
                       None if g is None else g.ctypes.data, n, out, st, err, rs, it, lm, mg,
@@ -191,6 +202,13 @@ class FBResult:
         (eigenvalue margins are relative, the others in pixels)."""
         return np.minimum(np.minimum(self.fwd.margin.min(axis=1), self.bwd.margin.min(axis=1)),
                           self.fb_margin)
+
+    def decision_margin(self, reason: int) -> np.ndarray:
+        """Per point, the smallest margin of the status decisions of one kind
+        (a LOST_* code) over both passes; LOST_INPUT decisions are exact."""
+        if reason == LOST_FB:
+            return self.fb_margin
+        return np.minimum(self.fwd.decision_margin(reason), self.bwd.decision_margin(reason))
 
 
 def track_fb(pI: Pyramid, pJ: Pyramid, pts, win=21, levels=None, max_iters=30, eps=0.01, min_eig=1e-4,

@@ -40,10 +40,14 @@
  *            Initial g_{L-1} = 0, or (guess - u) / 2^(L-1) when a guess is given.
  *   FB       ok = status_fwd & status_bwd & |p - back(fwd(p))|_2 <= thr.
  *
- * Per point it also reports the smallest margin seen on each threshold
- * decision (relative for the eigenvalue test, in pixels otherwise) so that a
- * status disagreement with a single-precision implementation can be
- * attributed to a decision taken within 1e-4 of its threshold.
+ * Per point it also reports, for each kind of threshold decision, the
+ * smallest margin by which that decision was taken (relative for the
+ * eigenvalue test, in pixels otherwise), so that a status disagreement with a
+ * single-precision implementation can be attributed to the decision that
+ * produced it being taken within 1e-4 of its threshold: the eigenvalue test
+ * at every level examined, the image-bound test at every evaluation, and the
+ * convergence test both over every iteration and at the deciding iterations
+ * only (those that stopped a level's loop).
  */
 #include <math.h>
 #include <stdint.h>
@@ -143,8 +147,10 @@ static double dmin(double a, double b) { return a < b ? a : b; }
  *   iters   [n]    Newton iterations summed over levels
  *   iters_level [n][levels] (may be NULL) Newton iterations at each level
  *   lmin    [n]    normalised lambda_min of G at the last level examined
- *   margin  [n][3] smallest |lambda_min - min_eig| / min_eig, |  |eta| - eps |,
- *                  and distance to the image-bound tests
+ *   margin  [n][4] smallest |lambda_min - min_eig| / min_eig over the levels
+ *                  examined; smallest | |eta| - eps | over every iteration;
+ *                  smallest distance to the image-bound tests; smallest
+ *                  | |eta| - eps | at the iterations that stopped a level
  */
 void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, const double *pts,
                const double *guess, int n, double *out, uint8_t *status, double *err, uint8_t *reason,
@@ -155,7 +161,7 @@ void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, co
     double *TX = T + N, *TY = T + 2 * N;
     for (int p = 0; p < n; ++p) {
         const double ux0 = pts[2 * p], uy0 = pts[2 * p + 1];
-        double m_eig = INFINITY, m_conv = INFINITY, m_bnd = INFINITY, lm = NAN;
+        double m_eig = INFINITY, m_conv = INFINITY, m_bnd = INFINITY, m_stop = INFINITY, lm = NAN;
         int st = 1, rs = ORC_OK, it = 0;
         double gx = 0.0, gy = 0.0, nux = 0.0, nuy = 0.0;
         double ex = 0.0, ey = 0.0;
@@ -225,8 +231,12 @@ void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, co
                 nuy += ey;
                 ++it;
                 if (iters_level) ++iters_level[(size_t)p * L + l];
-                m_conv = dmin(m_conv, fabs(sqrt(ex * ex + ey * ey) - prm->eps));
-                if (ex * ex + ey * ey < prm->eps * prm->eps) break;
+                const double step = fabs(sqrt(ex * ex + ey * ey) - prm->eps);
+                m_conv = dmin(m_conv, step);
+                if (ex * ex + ey * ey < prm->eps * prm->eps) {
+                    m_stop = dmin(m_stop, step);
+                    break;
+                }
             }
             if (l > 0) {
                 gx = 2.0 * (gx + nux);
@@ -265,9 +275,10 @@ void orc_track(const orc_level *I, const orc_level *J, const orc_params *prm, co
         err[p] = st ? e : 0.0;
         iters[p] = it;
         lmin[p] = lm;
-        margin[3 * p] = m_eig;
-        margin[3 * p + 1] = m_conv;
-        margin[3 * p + 2] = m_bnd;
+        margin[4 * p] = m_eig;
+        margin[4 * p + 1] = m_conv;
+        margin[4 * p + 2] = m_bnd;
+        margin[4 * p + 3] = m_stop;
     }
     free(T);
 }

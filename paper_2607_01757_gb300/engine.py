@@ -39,7 +39,7 @@ class StreamState:
     in_right: object = None
     kp_t: object = None  # device float2 [n_max]: points tracked prev -> cur
     kp_s: object = None  # device float2 [n_max]: points tracked left -> right
-    out_t: tuple = ()  # (pts, status, err)
+    out_t: tuple = ()  # (pts, status, err, reason)
     out_s: tuple = ()
     rig: object = None  # vt.StereoRig of a gated stereo stream
     gate_out: tuple = ()  # (status uint8 [n_max], xyz float [n_max, 3], reason uint8 [n_max])
@@ -61,12 +61,13 @@ class BatchedTracker:
         self.grad_type = grad_type
         self.gate = gate
         self.streams = []
-        # every stream's outputs are slices of three contiguous buffers, so one
+        # every stream's outputs are slices of four contiguous buffers, so one
         # copy each brings a whole step's results to the host
         total = sum(sp.n_kp * (2 if sp.stereo else 1) for sp in specs)
         self.out_pts = torch.zeros((max(1, total), 2), dtype=torch.float32, device=device)
         self.out_st = torch.zeros(max(1, total), dtype=torch.uint8, device=device)
         self.out_err = torch.zeros(max(1, total), dtype=torch.float32, device=device)
+        self.out_rs = torch.zeros(max(1, total), dtype=torch.uint8, device=device)  # VT_LOST_* per point
         off = 0
         for j, sp in enumerate(specs):
             s = StreamState(sp.sid, sp.w, sp.h, sp.levels, sp.stereo, sp.n_kp)
@@ -77,7 +78,7 @@ class BatchedTracker:
             s.kp_t = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device)
             s.kp_s = torch.zeros((sp.n_kp, 2), dtype=torch.float32, device=device) if sp.stereo else None
             def mk(o, n=sp.n_kp):
-                return self.out_pts[o:o + n], self.out_st[o:o + n], self.out_err[o:o + n]
+                return self.out_pts[o:o + n], self.out_st[o:o + n], self.out_err[o:o + n], self.out_rs[o:o + n]
 
             s.out_t = mk(off)
             off += sp.n_kp
@@ -119,12 +120,12 @@ class BatchedTracker:
                 fl = flops[k][0] if flops is not None else None
                 pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
                 tasks.append(vt.track_task(prev, cur, pts, s.out_t[0], s.out_t[1], s.out_t[2], fb=True, flops=fl,
-                                           levels=s.levels))
+                                           levels=s.levels, reason=s.out_t[3]))
             if s.stereo and n_s[k] > 0:
                 fl = flops[k][1] if flops is not None else None
                 pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
                 tasks.append(vt.track_task(cur, s.pyr_r, pts, s.out_s[0], s.out_s[1], s.out_s[2], fb=True, flops=fl,
-                                           levels=s.levels))
+                                           levels=s.levels, reason=s.out_s[3]))
                 if s.rig is not None and gate:
                     g = s.gate_out
                     gates.append(vt.gate_task(pts, s.out_s[0], s.rig, g[0], status_in=s.out_s[1], xyz=g[1],
@@ -170,10 +171,12 @@ class BatchedTracker:
                 self._build(right[k] if right is not None else s.in_right, s.levels, stream, s.pyr_r)
             if n_t[k] > 0:
                 pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
-                vt.vt_klt_track_fb(prev, cur, pts, prm, s.out_t[0], s.out_t[1], s.out_t[2], stream=stream)
+                vt.vt_klt_track_fb(prev, cur, pts, prm, s.out_t[0], s.out_t[1], s.out_t[2], reason=s.out_t[3],
+                                   stream=stream)
             if s.stereo and n_s[k] > 0:
                 pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
-                vt.vt_klt_track_fb(cur, s.pyr_r, pts, prm, s.out_s[0], s.out_s[1], s.out_s[2], stream=stream)
+                vt.vt_klt_track_fb(cur, s.pyr_r, pts, prm, s.out_s[0], s.out_s[1], s.out_s[2], reason=s.out_s[3],
+                                   stream=stream)
                 if s.rig is not None and gate:
                     g = s.gate_out
                     vt.vt_stereo_gate(pts, s.out_s[0], s.rig, self.gate, g[0], status_in=s.out_s[1], xyz_out=g[1],

@@ -1,39 +1,61 @@
 """Comparison rules between the CUDA path and the FP64 oracle.
 
 Flow: for points both sides track, |gpu - oracle| <= 0.01 px for 99.9 % of
-them and <= 0.05 px for all.  Status: a disagreement is accepted only where
-the oracle took one of its threshold decisions within 1e-4 of the threshold
-(relative for the eigenvalue test, in pixels for the convergence, image-bound
-and forward-backward tests)."""
+them and <= 0.05 px for all.
+
+Status: a disagreement is excused only by the decision that produced it: the
+kind of test named by the losing side's reason (the GPU's reason when the GPU
+lost the point, the oracle's when the oracle did) must have been taken by
+the oracle within 1e-4 of its threshold -- relative for the eigenvalue test,
+in pixels for the image-bound and forward-backward tests.  An input rejection
+is exact and never excused.  At most 0.1 % of the points may be excused."""
 
 from __future__ import annotations
 
 import numpy as np
 
+import oracle
+
 FLOW_TOL_999 = 0.01
 FLOW_TOL_MAX = 0.05
 MARGIN = 1e-4
+MAX_EXCUSED_FRAC = 0.001
 
 
-def oracle_margin(res) -> np.ndarray:
-    """Smallest decision margin per point of an oracle TrackResult / FBResult."""
-    if hasattr(res, "min_margin"):
-        return res.min_margin()
-    return res.margin.min(axis=1)
+def _decision_margins(ref):
+    return {r: ref.decision_margin(r) for r in (oracle.LOST_EIG, oracle.LOST_OOB, oracle.LOST_FB)}
 
 
-def compare(gpu_pts, gpu_status, ref_pts, ref_status, ref_margin, label=""):
+def compare(gpu_pts, gpu_status, gpu_reason, ref, label="", idx=None):
+    """Compare GPU results with an oracle TrackResult or FBResult (forward
+    positions for FB).  ``idx`` selects the GPU entries that correspond to the
+    oracle's points (a sample re-tracked by the oracle)."""
     gpu_pts = np.asarray(gpu_pts, np.float64).reshape(-1, 2)
-    ref_pts = np.asarray(ref_pts, np.float64).reshape(-1, 2)
-    gs = np.asarray(gpu_status).astype(bool)
-    rs = np.asarray(ref_status).astype(bool)
+    gpu_status = np.asarray(gpu_status)
+    gpu_reason = np.asarray(gpu_reason)
+    if idx is not None:
+        gpu_pts, gpu_status, gpu_reason = gpu_pts[idx], gpu_status[idx], gpu_reason[idx]
+    fb = hasattr(ref, "fwd")
+    ref_pts = np.asarray(ref.fwd.pts if fb else ref.pts, np.float64).reshape(-1, 2)
+    gs = gpu_status.astype(bool)
+    rs = np.asarray(ref.status).astype(bool)
+    assert len(gs) == len(rs), (label, len(gs), len(rs))
+    margins = _decision_margins(ref)
     mism = np.nonzero(gs != rs)[0]
-    bad = [int(i) for i in mism if not (ref_margin[i] < MARGIN)]
-    assert not bad, f"{label}: status mismatch outside the margin rule at {bad[:10]} (margins {ref_margin[bad[:10]]})"
+    bad = []
+    for i in mism:
+        why = int(gpu_reason[i]) if not gs[i] else int(ref.reason[i])
+        m = margins[why][i] if why in margins else np.inf
+        if not (m < MARGIN):
+            bad.append((int(i), why, float(m)))
+    assert not bad, f"{label}: status mismatch not excused by its own decision's margin (index, reason, margin): " \
+                    f"{bad[:10]}"
+    n = len(gs)
+    assert len(mism) <= MAX_EXCUSED_FRAC * n, f"{label}: {len(mism)} of {n} points excused by the margin rule"
     both = gs & rs
     d = np.hypot(*(gpu_pts[both] - ref_pts[both]).T) if both.any() else np.zeros(0)
     stats = {
-        "n": int(len(gs)),
+        "n": int(n),
         "tracked_gpu": int(gs.sum()),
         "tracked_ref": int(rs.sum()),
         "status_mismatch": int(len(mism)),

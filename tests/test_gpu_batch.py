@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare, oracle_margin
+from parity import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -116,7 +116,7 @@ def test_batched_pyramids_bit_exact_and_tracking_matches():
             assert torch.equal(out[ok], o[0][ok])
             r = oracle.track_fb(oracle.build_pyramid(I, prm.levels), oracle.build_pyramid(J, prm.levels), kpn,
                                 prm.win, prm.levels, prm.max_iters, prm.eps, prm.min_eig, prm.fb_thr)
-            compare(o[0].cpu().numpy(), o[1].cpu().numpy(), r.fwd.pts, r.status, oracle_margin(r), "batched")
+            compare(o[0].cpu().numpy(), o[1].cpu().numpy(), o[3].cpu().numpy(), r, "batched")
     b.free()
 
 

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare, oracle_margin
+from parity import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -31,9 +31,10 @@ def _gpu_fb(I, J, pts, prm, grad):
     out = torch.zeros((n, 2), device="cuda")
     st = torch.zeros(n, dtype=torch.uint8, device="cuda")
     err = torch.zeros(n, device="cuda")
-    vt.vt_klt_track_fb(pI, pJ, p0, prm, out, st, err)
+    rs = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    vt.vt_klt_track_fb(pI, pJ, p0, prm, out, st, err, reason=rs)
     torch.cuda.synchronize()
-    res = out.cpu().numpy(), st.cpu().numpy(), err.cpu().numpy()
+    res = out.cpu().numpy(), st.cpu().numpy(), err.cpu().numpy(), rs.cpu().numpy()
     pI.free()
     pJ.free()
     return res
@@ -52,9 +53,9 @@ def test_stereo_temporal_sequence_752x480():
     for I, J, pts, label in [(seq.left[0], seq.left[1], seq.kps[0], "temporal"),
                              (seq.left[1], seq.right[1], seq.kps[1], "stereo")]:
         assert len(pts) == 1000
-        g_pts, g_st, g_err = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
+        g_pts, g_st, g_err, g_rs = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
         r = _oracle_fb(I, J, pts, prm)
-        st = compare(g_pts, g_st, r.fwd.pts, r.status, oracle_margin(r), label)
+        st = compare(g_pts, g_st, g_rs, r, label)
         assert st["tracked_ref"] > 500, st
 
 
@@ -70,9 +71,9 @@ def test_precision_workload_1280x1024_int16(precision_seq):
     prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
     I, J, pts = seq.left[0], seq.left[1], seq.kps[0]
     assert len(pts) == 2000
-    g_pts, g_st, _ = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
+    g_pts, g_st, _, g_rs = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_S16)
     r = _oracle_fb(I, J, pts, prm)
-    compare(g_pts, g_st, r.fwd.pts, r.status, oracle_margin(r), "1280x1024 int16")
+    compare(g_pts, g_st, g_rs, r, "1280x1024 int16")
 
 
 def test_precision_workload_fp16_gradients_error_stated(precision_seq):
@@ -87,7 +88,7 @@ def test_precision_workload_fp16_gradients_error_stated(precision_seq):
     seq = precision_seq
     prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
     I, J, pts = seq.left[0], seq.left[1], seq.kps[0]
-    g_pts, g_st, _ = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_F16)
+    g_pts, g_st, _, _ = _gpu_fb(I, J, pts, prm, vt.VT_GRAD_F16)
     r = _oracle_fb(I, J, pts, prm)
     both = (g_st == 1) & (r.status == 1)
     d = np.hypot(*(g_pts[both] - r.fwd.pts[both]).T)
@@ -145,8 +146,8 @@ def test_full_size_streams_batched_sampled(warps):
         for I, J, kp, out in tasks:
             idx = np.sort(rng.choice(len(kp), size=min(48, len(kp)), replace=False))
             r = _oracle_fb(I, J, kp[idx], prm_s)
-            compare(out[0].cpu().numpy()[idx], out[1].cpu().numpy()[idx], r.fwd.pts, r.status, oracle_margin(r),
-                    f"{sp.w}x{sp.h} L{sp.levels}")
+            compare(out[0].cpu().numpy(), out[1].cpu().numpy(), out[3].cpu().numpy(), r, f"{sp.w}x{sp.h} L{sp.levels}",
+                    idx=idx)
     tr.free()
 
 
@@ -181,6 +182,6 @@ def test_stereo_temporal_sequence_six_frames_batched():
         for I, J, kp, out, label in tasks:
             idx = np.sort(rng.choice(len(kp), size=120, replace=False))
             r = _oracle_fb(I, J, kp[idx], vt.KltParams(win=21, levels=5))
-            compare(out[0].cpu().numpy()[idx], out[1].cpu().numpy()[idx], r.fwd.pts, r.status, oracle_margin(r),
-                    f"frame {t} {label}")
+            compare(out[0].cpu().numpy(), out[1].cpu().numpy(), out[3].cpu().numpy(), r, f"frame {t} {label}",
+                    idx=idx)
     tr.free()

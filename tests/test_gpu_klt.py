@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare, oracle_margin
+from parity import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -52,8 +52,7 @@ def _ref(I, J, pts, prm, fb=False, guess=None):
 
 
 def _check(g, r, label, fb=False):
-    pts_ref = r.fwd.pts if fb else r.pts
-    st = compare(g["pts"], g["status"], pts_ref, r.status, oracle_margin(r), label)
+    st = compare(g["pts"], g["status"], g["reason"], r, label)
     both = (g["status"] == 1) & (r.status == 1)
     err_ref = r.fwd.err if fb else r.err
     np.testing.assert_allclose(g["err"][both], err_ref[both], rtol=2e-3, atol=2e-3)
@@ -109,6 +108,44 @@ def test_fused_fb_equals_separate_calls(cfg1):
     assert torch.equal(u_st, fb_st)
     ok = u_st.bool()
     assert (u_out[ok] - f_out[ok]).abs().max().item() <= 1e-5
+
+
+@pytest.mark.parametrize("with_guess", [False, True])
+def test_plain_klt_track_entry_point(cfg1, with_guess):
+    """vt_klt_track, the plain call of the boundary (no diagnostics, default
+    eigenvalue threshold 1e-4), on config 1 with and without pts_guess (the
+    ground-truth positions offset by a seeded error of up to 2 px): equal to
+    vt_klt_track_ex on the same inputs bit for bit, and within parity of the
+    oracle (the status rule reads the reasons _ex reports)."""
+    import torch
+
+    vt = _vt()
+    pI = vt.vt_pyramid_build_grad(cfg1.I, 4)
+    pJ = vt.vt_pyramid_build_grad(cfg1.J, 4)
+    n = len(cfg1.pts)
+    p0 = torch.from_numpy(np.ascontiguousarray(cfg1.pts, np.float32)).cuda()
+    guess_h = None
+    g = None
+    if with_guess:
+        rng = np.random.Generator(np.random.PCG64(71))
+        guess_h = (cfg1.gt + rng.uniform(-2.0, 2.0, cfg1.gt.shape)).astype(np.float32)
+        g = torch.from_numpy(guess_h).cuda()
+    out, st, err = torch.zeros((n, 2), device="cuda"), torch.zeros(n, dtype=torch.uint8, device="cuda"), \
+        torch.zeros(n, device="cuda")
+    vt.vt_klt_track(pI, pJ, p0, out, st, err, pts_guess=g, win=21, levels=4, max_iters=30, eps=0.01)
+    prm = vt.KltParams(win=21, levels=4, max_iters=30, eps=0.01, min_eig=1e-4)
+    o2, s2, e2 = torch.zeros_like(out), torch.zeros_like(st), torch.zeros_like(err)
+    rs = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    vt.vt_klt_track_ex(pI, pJ, p0, prm, o2, s2, e2, pts_guess=g, reason=rs)
+    torch.cuda.synchronize()
+    assert torch.equal(st, s2) and torch.equal(out, o2) and torch.equal(err, e2)
+    r = _ref(cfg1.I, cfg1.J, cfg1.pts, prm, guess=None if guess_h is None else guess_h.astype(np.float64))
+    stats = compare(out.cpu().numpy(), st.cpu().numpy(), rs.cpu().numpy(), r, f"vt_klt_track guess={with_guess}")
+    assert stats["tracked_ref"] >= 140, stats
+    both = (st.cpu().numpy() == 1) & (r.status == 1)
+    np.testing.assert_allclose(err.cpu().numpy()[both], r.err[both], rtol=2e-3, atol=2e-3)
+    pI.free()
+    pJ.free()
 
 
 @pytest.mark.parametrize("win", [9, 15, 31])
