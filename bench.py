@@ -34,14 +34,63 @@ if ROOT not in sys.path:
 METRIC = "tracked features/s & p99 frame latency, batched/served vs plain KLT, 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
-# DRAM bytes (read + write) per launch from one ncu capture of the default
-# workload with the current kernels (32 streams, 4 frames, seed 4;
-# dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before each
-# captured launch, mean of two captured steps), summarised in
-# profiles/launches_bench_32streams.md.  Reported only for that workload.
-NCU_TRAFFIC_BYTES = {"k_klt_batch": 439.43e6 + 1.24e6, "pyramid": 83.19e6 + 271.38e6}
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
+# one ncu capture of the default workload (32 streams, 4 frames, seed 4;
+# caches flushed before each captured launch), with the date of the capture
+# and a hash of the kernel sources it measured.  A figure is reported only
+# for that workload and only while the sources still hash the same: a kernel
+# changed since the capture reports null.
+NCU_CAPTURES = {
+    "k_klt_batch": {"bytes": None, "date": None, "sources_sha1": None},
+    "pyramid": {"bytes": None, "date": None, "sources_sha1": None},
+}
+KERNEL_SOURCES = {
+    "k_klt_batch": ["vt_klt.cuh", "vt_batch.cu", "vt_internal.cuh"],
+    "pyramid": ["vt_pyramid.cu", "vt_internal.cuh"],
+}
+
+
+def sources_sha1(kernel):
+    """SHA-1 over the CUDA sources a kernel is built from (in order)."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2607_01757_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel, default_workload):
+    """(bytes, note) of the committed ncu capture of `kernel`, or (None, why)."""
+    c = NCU_CAPTURES[kernel]
+    if not default_workload:
+        return None, "captured on the default workload only"
+    if c["bytes"] is None:
+        return None, "no capture of the current kernel"
+    if c["sources_sha1"] != sources_sha1(kernel):
+        return None, f"kernel changed since the capture of {c['date']}"
+    return c["bytes"], f"one ncu capture ({c['date']}), cold caches, default workload"
+
+
+def measure_fp32_peak(torch, stream):
+    """FP32 FMA throughput of this device (TFLOP/s): the library's FMA-chain
+    probe, best of 10 launches after 3 warm-ups, CUDA events on `stream`."""
+    import paper_2607_01757_gb300 as vt
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = torch.empty(sms * 2048, dtype=torch.float32, device="cuda")
+    best, iters = 0.0, 2048
+    for i in range(13):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = vt.vt_fp32_fma_probe(iters, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best, sms
 
 
 def parse():
@@ -326,15 +375,19 @@ def run_native(a, rank, world, local_rank):
         e.record(stream)  # torch creates the CUDA event on first record
         return e
 
-    klt_ms, pyr_ms = [], []
+    klt_ms, pyr_ms, lev_ms = [], [], []
     for i in range(a.steps):
         flush.fill_(i & 0xFF)
-        e = [ev(), ev(), ev(), ev()]
-        batched_step(t, events=e)
+        batched_prepare(t)
+        n_pyr = vt.vt_batch_info(tr.batch)["launches_per_run"] - 1
+        e = [ev() for _ in range(4 + n_pyr)]
+        vt.vt_batch_run_levels_timed(tr.batch, stream, e)
+        tr.advance(sids)
         t += 1
         torch.cuda.synchronize()
         pyr_ms.append(e[0].elapsed_time(e[1]))
         klt_ms.append(e[2].elapsed_time(e[3]))
+        lev_ms.append([e[0].elapsed_time(e[4])] + [e[4 + j - 1].elapsed_time(e[4 + j]) for j in range(1, n_pyr)])
     # algorithmic FLOPs of the tracking launch, per distinct step of the period
     P = max(1, 2 * (F - 1))
     flops_per_step = []
@@ -358,28 +411,16 @@ def run_native(a, rank, world, local_rank):
         batched_step(t)
         t += 1
         torch.cuda.synchronize()
+    fp32_peak, sm_count = measure_fp32_peak(torch, stream)
     clocks = clk.stop()
     klt_flops = statistics.mean(flops_per_step)
     klt_avg_s = statistics.mean(klt_ms) / 1e3
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_derived = sm_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = klt_flops / klt_avg_s / 1e12
-    # pyramid algorithmic bytes (fused build): per level l of a frame, read
-    # level l (the caller image for l = 0), write level l+1, write 4 B/px of
-    # gradients, and for l = 0 write the level-0 copy
-    pyr_bytes = 0
-    for s in tr.streams:
-        w, h = s.w, s.h
-        dims = []
-        for _ in range(s.levels):
-            dims.append((w, h))
-            w, h = (w + 1) // 2, (h + 1) // 2
-        b = dims[0][0] * dims[0][1]  # level-0 copy
-        for l, (lw, lh) in enumerate(dims):
-            b += lw * lh + (0 if grad_type == vt.VT_GRAD_NONE else 4) * lw * lh
-            if l + 1 < len(dims):
-                b += dims[l + 1][0] * dims[l + 1][1]
-        pyr_bytes += b * (2 if s.stereo else 1)
+    pyr_launch_bytes = pyramid_launch_bytes(tr.streams, grad_type != vt.VT_GRAD_NONE, vt)
+    pyr_bytes = sum(pyr_launch_bytes)
     pyr_avg_s = statistics.mean(pyr_ms) / 1e3
+    lev_avg_ms = [statistics.mean(x[j] for x in lev_ms) for j in range(len(lev_ms[0]))]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -387,7 +428,8 @@ def run_native(a, rank, world, local_rank):
     except OSError:
         pass
     default_wl = (a.streams, a.frames, a.seed, a.grad) == (32, 4, 4, "s16") and world == 1
-    traffic = NCU_TRAFFIC_BYTES if default_wl else {}
+    klt_traffic, klt_traffic_note = captured_traffic("k_klt_batch", default_wl)
+    pyr_traffic, pyr_traffic_note = captured_traffic("pyramid", default_wl)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
@@ -684,16 +726,21 @@ def run_native(a, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": a.steps * launches_per_step,
         "roofline": {"bound": "alu", "kernel": "k_klt_batch", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic.get("k_klt_batch"),
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": klt_traffic,
                      "flops_per_launch": klt_flops, "launch_ms": klt_avg_s * 1e3,
-                     "traffic_note": "DRAM bytes per launch, one ncu capture (cold caches), default workload only",
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     "traffic_note": klt_traffic_note,
+                     "peak_note": f"measured: FP32 FMA-chain probe (vt_fp32_fma_probe) on {sm_count} SMs, best of "
+                                  f"10 launches, CUDA events (derived {fp32_derived:.1f} TFLOP/s = {sm_count} SMs x "
+                                  f"128 lanes x 2 x 2.07 GHz)"},
         "roofline_pyramid": {"bound": "hbm", "kernel": "k_pyr_batch+k_pyr_tail", "achieved": pyr_bytes / pyr_avg_s
                              / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": traffic.get("pyramid"),
+                             "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": pyr_traffic,
                              "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src,
-                             "traffic_note": "DRAM bytes of the step's pyramid launches, one ncu capture (cold "
-                                             "caches), default workload only"},
+                             "per_launch": [{"launch": ("tail" if j == len(lev_avg_ms) - 1 else f"level {j}"),
+                                             "ms": lev_avg_ms[j], "bytes": pyr_launch_bytes[j],
+                                             "gbs": pyr_launch_bytes[j] / (lev_avg_ms[j] / 1e3) / 1e9}
+                                            for j in range(len(lev_avg_ms))],
+                             "traffic_note": pyr_traffic_note},
         "served": served,
         "gftt": gftt,
         "stereo_gate": gate,
@@ -803,6 +850,38 @@ def run_gftt(specs, frames):
         g.free()
         p.free()
     return out
+
+
+def pyramid_launch_bytes(streams, grad, vt):
+    """Algorithmic bytes of each pyramid launch of a batched step (tiled
+    launches of levels 0, 1, .., then the tail launch): a tiled launch l reads
+    level l of every frame whose tail starts above l (the caller's image for
+    l = 0), writes level l+1 and, with gradients, 4 B/px of level l's planes;
+    the tail reads the frame's first tail level c and writes every smaller
+    level and the planes of c and below.  Level 0 also writes the pyramid's
+    level-0 copy unless the frame is built in place."""
+    tail_max = 40960
+    per = {}
+    for s in streams:
+        dims, w, h = [], s.w, s.h
+        for _ in range(s.levels):
+            dims.append((w, h))
+            w, h = (w + 1) // 2, (h + 1) // 2
+        c = next((l for l, (lw, lh) in enumerate(dims) if ((lw + 63) // 64 * 64) * lh <= tail_max), len(dims) - 1)
+        gb = 4 if grad else 0
+        for _ in range(2 if s.stereo else 1):
+            for l in range(c):
+                lw, lh = dims[l]
+                b = lw * lh + dims[l + 1][0] * dims[l + 1][1] + gb * lw * lh
+                if l == 0 and not getattr(s, "in_place", False):
+                    b += lw * lh
+                per[l] = per.get(l, 0) + b
+            b = dims[c][0] * dims[c][1] * (2 if c == 0 and not getattr(s, "in_place", False) else 1)
+            for l in range(c, len(dims)):
+                b += gb * dims[l][0] * dims[l][1] + (dims[l][0] * dims[l][1] if l > c else 0)
+            per["tail"] = per.get("tail", 0) + b
+    nt = max([k for k in per if k != "tail"], default=-1) + 1
+    return [per.get(l, 0) for l in range(nt)] + [per.get("tail", 0)]
 
 
 def cpu_model() -> str:

@@ -155,8 +155,9 @@ vt_status launch_gate_batch(const uint8_t *dev_tab, int grid, cudaStream_t s);
 bool gate_args_ok(const vt_stereo_rig *rig, const vt_gate_params *prm);
 
 // Host helpers implemented in vt_pyramid.cu.
+// `ev` (nullable): one event recorded after each launch (tiled_launches + 1).
 vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,
-                           cudaStream_t s);
+                           cudaStream_t s, cudaEvent_t *ev = nullptr);
 int tail_start_level(const vt_pyramid *p);
 int tail_parts(const vt_pyramid *p);
 int pyr_batch_blocks_per_sm();

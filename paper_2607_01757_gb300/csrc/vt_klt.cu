@@ -166,3 +166,48 @@ vt_status vt_fb_check(const float *p0, const float *p0_back, const uint8_t *st_f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput probe: the denominator of the tracking kernel's
+// roofline is this device's measured FMA rate rather than a data-sheet figure.
+// Every thread runs 8 independent FMA chains (enough independent work per
+// warp to keep the FMA pipes issuing at full occupancy), 8 x iters FMAs of
+// 2 FLOPs each, and writes one sum so nothing is optimised away.
+namespace vt {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeCtasPerSm = 8;  // 2048 threads per SM
+
+__global__ void __launch_bounds__(kProbeThreads) k_fma_probe(float *out, int iters, float m, float c) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, c);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace vt
+
+extern "C" vt_status vt_fp32_fma_probe(int iters, float *out, long long out_floats, long long *flops,
+                                       void *cuda_stream) {
+    int dev = 0, sms = 0;
+    if (iters < 1 || !out || !flops || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_ARG;
+    }
+    const long long grid = (long long)sms * kProbeCtasPerSm;
+    if (out_floats < grid * kProbeThreads) return VT_ERR_ARG;
+    vt::k_fma_probe<<<(int)grid, kProbeThreads, 0, (cudaStream_t)cuda_stream>>>(out, iters, 0.999f, 1e-3f);
+    *flops = grid * kProbeThreads * 8LL * 8LL * iters * 2LL;
+    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+}

@@ -532,7 +532,7 @@ __host__ __device__ int scharr_tiles(int w, int h, int &tiles_x) {
 }
 
 vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype, int grid_pyr, int grid_tail,
-                           cudaStream_t s) {
+                           cudaStream_t s, cudaEvent_t *ev) {
     static const bool attr = [] {  // once, thread-safe static initialisation
         return cudaFuncSetAttribute(k_pyr_tail<VT_GRAD_S16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     TAIL_SMEM) == cudaSuccess &&
@@ -549,6 +549,7 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
             k_pyr_batch<VT_GRAD_NONE><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
         else
             k_pyr_batch<VT_GRAD_S16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
+        if (ev && ev[l]) cudaEventRecord(ev[l], s);
     }
     if (gtype == VT_GRAD_F16)
         k_pyr_tail<VT_GRAD_F16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
@@ -556,6 +557,7 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
         k_pyr_tail<VT_GRAD_NONE><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
     else
         k_pyr_tail<VT_GRAD_S16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
+    if (ev && ev[tiled_launches]) cudaEventRecord(ev[tiled_launches], s);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 

@@ -126,6 +126,19 @@ def vt_version() -> str:
     return _lib.vt_version().decode()
 
 
+_sig("vt_fp32_fma_probe", i32, [i32, vp, C.c_longlong, C.POINTER(C.c_longlong), vp])
+
+
+def vt_fp32_fma_probe(iters: int, out, stream=None) -> int:
+    """Launch the FP32 FMA throughput probe (a measurement helper); returns
+    the launch's FLOP count.  ``out``: device float32 tensor of at least
+    SMs x 2048 entries."""
+    fl = C.c_longlong()
+    _check(_lib.vt_fp32_fma_probe(int(iters), _ptr(out), int(out.numel()), C.byref(fl), _stream(stream)),
+           "vt_fp32_fma_probe")
+    return int(fl.value)
+
+
 class Pyramid:
     """Owning handle of a library pyramid (vt_pyramid*)."""
 
@@ -397,6 +410,15 @@ def vt_batch_run_graph(b: Batch, stream=None) -> None:
 def vt_batch_run_timed(b: Batch, stream=None, ev_pyr0=None, ev_pyr1=None, ev_klt0=None, ev_klt1=None) -> None:
     _check(_lib.vt_batch_run_timed(b, _stream(stream), _event_handle(ev_pyr0), _event_handle(ev_pyr1),
                                    _event_handle(ev_klt0), _event_handle(ev_klt1)), "vt_batch_run_timed")
+
+
+_sig("vt_batch_run_levels_timed", i32, [vp, vp, C.POINTER(vp), i32])
+
+
+def vt_batch_run_levels_timed(b: Batch, stream, events) -> None:
+    """events: 4 + pyramid-launch CUDA events (see vt.h); None entries skipped."""
+    arr = (vp * len(events))(*[_event_handle(e) for e in events])
+    _check(_lib.vt_batch_run_levels_timed(b, _stream(stream), arr, len(events)), "vt_batch_run_levels_timed")
 
 
 def vt_batch_info(b: Batch):
