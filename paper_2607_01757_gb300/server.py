@@ -14,7 +14,13 @@ and keypoints in pinned host memory).  The loop:
   slots alternate, so a batch is assembled and launched while the previous
   one still runs and their work overlaps on the device;
 * completes a request when its slot's event has fired, recording the latency
-  from the request's arrival time to the moment its results are on the host.
+  from the request's arrival time to the moment all its results (temporal
+  and, for a stereo stream, left->right points and status) are on the host.
+
+A request's features are the previous frame's keypoints it tracks through
+the whole step (forward-backward temporal tracking, plus the left->right
+check of the new frame's keypoints on a stereo stream), as in the batched
+benchmark; the stereo pairs are counted separately.
 
 The plain baseline serves the same trace one request at a time with the
 single-pair calls.
@@ -39,6 +45,7 @@ class Request:
     t_arrive: float  # seconds from the trace start
     t_done: float = -1.0
     n_features: int = 0
+    n_stereo: int = 0
 
 
 @dataclass
@@ -46,6 +53,7 @@ class ServeStats:
     served: int
     features: int
     wall_s: float
+    stereo_pairs: int = 0
     latencies_ms: list = field(default_factory=list)
     batches: int = 0
     mean_batch: float = 0.0
@@ -59,6 +67,7 @@ class ServeStats:
         return {
             "requests": self.served,
             "features_per_s": self.features / self.wall_s if self.wall_s > 0 else 0.0,
+            "stereo_pairs_per_s": self.stereo_pairs / self.wall_s if self.wall_s > 0 else 0.0,
             "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),
             "p999_ms": float(np.percentile(lat, 99.9)),
@@ -118,8 +127,12 @@ class Server:
         self.h_left = [[pin(x) for x in fr.left] for fr in frames]
         self.h_right = [[pin(x) if x is not None else None for x in fr.right] for fr in frames]
         self.h_kps = [[pin(k) for k in fr.kps] for fr in frames]
-        self.h_out = [(torch.empty((s.n_max, 2), dtype=torch.float32).pin_memory(),
-                       torch.empty(s.n_max, dtype=torch.uint8).pin_memory()) for s in self.tr.streams]
+        # host results per stream: temporal points and status, then (stereo)
+        # left->right points and status
+        self.h_out = [tuple(t for _ in range(2 if s.stereo else 1)
+                            for t in (torch.empty((s.n_max, 2), dtype=torch.float32).pin_memory(),
+                                      torch.empty(s.n_max, dtype=torch.uint8).pin_memory()))
+                      for s in self.tr.streams]
         self.footprint = [self._footprint(i) for i in range(self.S)]
         self.slots = [dict(stream=torch.cuda.Stream(), event=torch.cuda.Event(), batch=vt.Batch(
             self.tr.batch_capacity[0], self.tr.batch_capacity[1]), reqs=None) for _ in range(slots)]
@@ -155,6 +168,7 @@ class Server:
                 n_t.append(nt)
                 n_s.append(ns)
                 r.n_features = nt
+                r.n_stereo = ns
             fa, nf, ta, ntk, gates = tr.step_tables(sids, n_t, n_s)
             code = vt._lib.vt_batch_set(slot["batch"], fa, nf, tr.grad_type, ta, ntk, vt.C.byref(self.params.c()))
             if code != vt.VT_OK:
@@ -163,13 +177,20 @@ class Server:
                 vt.vt_batch_set_gates(slot["batch"], gates, tr.gate)
             vt.vt_batch_run_graph(slot["batch"], cs)
             tr.advance(sids)
-            for r, nt in zip(reqs, n_t):
-                s = tr.streams[r.sid]
-                if nt:
-                    self.h_out[r.sid][0][:nt].copy_(s.out_t[0][:nt], non_blocking=True)
-                    self.h_out[r.sid][1][:nt].copy_(s.out_t[1][:nt], non_blocking=True)
+            for r, nt, ns in zip(reqs, n_t, n_s):
+                self._copy_out(r.sid, nt, ns)
             slot["event"].record(cs)
         slot["reqs"] = reqs
+
+    def _copy_out(self, sid, nt, ns):
+        """Queue the D2H copies of one request's results on the current stream."""
+        s, h = self.tr.streams[sid], self.h_out[sid]
+        if nt:
+            h[0][:nt].copy_(s.out_t[0][:nt], non_blocking=True)
+            h[1][:nt].copy_(s.out_t[1][:nt], non_blocking=True)
+        if ns:
+            h[2][:ns].copy_(s.out_s[0][:ns], non_blocking=True)
+            h[3][:ns].copy_(s.out_s[1][:ns], non_blocking=True)
 
     def serve(self, trace, realtime=True, max_batch=64, stall_s=60.0):
         """Run the trace; returns ServeStats.  With realtime=False every
@@ -230,6 +251,7 @@ class Server:
                         r.t_done = td
                         stats.latencies_ms.append((td - r.t_arrive) * 1e3)
                         stats.features += r.n_features
+                        stats.stereo_pairs += r.n_stereo
                         in_flight.discard(r.sid)
                         remaining[r.sid] -= 1
                         if remaining[r.sid] == 0:  # stream ended: free its budget
@@ -292,13 +314,12 @@ class Server:
                     s.kp_s[:ns].copy_(kq, non_blocking=True)
                 tr.plain_step([r.sid], [nt], [ns], stream=cs)
                 tr.advance([r.sid])
-                if nt:
-                    self.h_out[r.sid][0][:nt].copy_(s.out_t[0][:nt], non_blocking=True)
-                    self.h_out[r.sid][1][:nt].copy_(s.out_t[1][:nt], non_blocking=True)
+                self._copy_out(r.sid, nt, ns)
             cs.synchronize()
             td = now()
             stats.latencies_ms.append((td - r.t_arrive) * 1e3)
             stats.features += nt
+            stats.stereo_pairs += ns
             stats.served += 1
         stats.wall_s = now()
         stats.batches = stats.served

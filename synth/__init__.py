@@ -21,6 +21,8 @@ from .scenes import (
     HeightFieldScene,
     make_stereo_sequence,
     make_config3_pair,
+    make_config3_contrast_pair,
+    ContrastPair,
     StreamSpec,
     make_stream_mix,
     render_stream_frames,
@@ -37,6 +39,8 @@ __all__ = [
     "HeightFieldScene",
     "make_stereo_sequence",
     "make_config3_pair",
+    "make_config3_contrast_pair",
+    "ContrastPair",
     "StreamSpec",
     "make_stream_mix",
     "render_stream_frames",

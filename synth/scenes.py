@@ -170,11 +170,26 @@ class StereoSequence:
     gains: list
 
 
+def _render_stereo_frame(args):
+    """One frame of a stereo sequence (left, right, left depth, keypoints)."""
+    scene, R, C, CR, w, h, f, blur, g, kp_seed, n_kp, nms_radius = args
+    imL, dL = scene.render(R, C, w, h, f)
+    imR, _ = scene.render(R, CR, w, h, f)
+    if blur is not None:
+        imL = _motion_blur(imL, *blur)
+        imR = _motion_blur(imR, *blur)
+    L8 = quantize_u8((imL - 128.0) * g + 128.0 if g != 1.0 else imL)
+    R8 = quantize_u8((imR - 128.0) * g + 128.0 if g != 1.0 else imR)
+    return L8, R8, dL.astype(np.float32), select_keypoints_nms(L8, n_kp, kp_seed, radius=nms_radius)
+
+
 def make_stereo_sequence(seed: int = 2, n_frames: int = 4, w: int = 752, h: int = 480, n_kp: int = 1000,
                          f: float | None = None, baseline: float = 0.11, fps: float = 20.0,
                          max_speed: float = 0.3, max_rot_deg: float = 5.0, blur_max: float = 0.0,
                          gain_range: tuple[float, float] | None = None, nms_radius: int = 4,
-                         scene: HeightFieldScene | None = None) -> StereoSequence:
+                         scene: HeightFieldScene | None = None, map_fn=map) -> StereoSequence:
+    """``map_fn``: how the frames are rendered (e.g. a process pool's map);
+    the frames do not depend on it."""
     rng = np.random.Generator(np.random.PCG64(seed))
     if f is None:
         f = 460.0 * w / 752.0
@@ -189,30 +204,25 @@ def make_stereo_sequence(seed: int = 2, n_frames: int = 4, w: int = 752, h: int 
     Pr = rng.uniform(30.0, 90.0, 3)
     wr = rng.uniform(0.3, 1.0, 3) * per_axis_w
     phr = rng.uniform(0, 2 * np.pi, 3)
-    left, right, depth, kps, poses, gains = [], [], [], [], [], []
+    jobs, poses, gains = [], [], []
     for k in range(n_frames):
         C = vt * Pt / (2 * np.pi) * np.sin(2 * np.pi * k / Pt + pht)
         ang = wr * Pr / (2 * np.pi) * np.sin(2 * np.pi * k / Pr + phr)
         R = _rot(*ang)
         CR = C + R @ np.array([baseline, 0.0, 0.0])
-        imL, dL = scene.render(R, C, w, h, f)
-        imR, _ = scene.render(R, CR, w, h, f)
-        g = 1.0
+        blur = None
         if blur_max > 0:
             bl, ba = rng.uniform(0, blur_max), rng.uniform(0, np.pi)
-            imL = _motion_blur(imL, bl, ba)
-            imR = _motion_blur(imR, bl, ba)
+            blur = (bl, ba)
+        g = 1.0
         if gain_range is not None and k > 0:
             g = rng.uniform(*gain_range)
-        L8 = quantize_u8((imL - 128.0) * g + 128.0 if g != 1.0 else imL)
-        R8 = quantize_u8((imR - 128.0) * g + 128.0 if g != 1.0 else imR)
-        left.append(L8)
-        right.append(R8)
-        depth.append(dL.astype(np.float32))
-        kps.append(select_keypoints_nms(L8, n_kp, seed * 31 + k, radius=nms_radius))
+        jobs.append((scene, R, C, CR, w, h, f, blur, g, seed * 31 + k, n_kp, nms_radius))
         poses.append((R, C))
         gains.append(g)
-    return StereoSequence(left, right, depth, kps, poses, f, baseline, seed, gains)
+    out = list(map_fn(_render_stereo_frame, jobs))
+    return StereoSequence([o[0] for o in out], [o[1] for o in out], [o[2] for o in out], [o[3] for o in out],
+                          poses, f, baseline, seed, gains)
 
 
 def make_config3_pair(seed: int = 3, n_frames: int = 2, w: int = 1280, h: int = 1024, n_kp: int = 2000):
@@ -220,6 +230,76 @@ def make_config3_pair(seed: int = 3, n_frames: int = 2, w: int = 1280, h: int = 
     U[0.7, 1.3] on every frame after the first."""
     return make_stereo_sequence(seed=seed, n_frames=n_frames, w=w, h=h, n_kp=n_kp,
                                 blur_max=7.0, gain_range=(0.7, 1.3))
+
+
+def _render_polygons(w, h, polys, base=128.0, ss=4):
+    """Area-sampled rendering of filled convex polygons (painter's order) on
+    a constant background: each pixel is the mean of an ss x ss grid of
+    sub-samples, so edges are sharp (one pixel of transition) and exact."""
+    img = np.full((h, w), base, np.float64)
+    off = (np.arange(ss) + 0.5) / ss - 0.5
+    for verts, val in polys:
+        x0 = max(0, int(np.floor(verts[:, 0].min())) - 1)
+        x1 = min(w, int(np.ceil(verts[:, 0].max())) + 2)
+        y0 = max(0, int(np.floor(verts[:, 1].min())) - 1)
+        y1 = min(h, int(np.ceil(verts[:, 1].max())) + 2)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        sx = np.broadcast_to(xx[:, :, None, None] + off[None, None, None, :], xx.shape + (ss, ss))
+        sy = np.broadcast_to(yy[:, :, None, None] + off[None, None, :, None], xx.shape + (ss, ss))
+        inside = np.ones(sx.shape, bool)
+        n = len(verts)
+        area = 0.0
+        for k in range(n):
+            (ax, ay), (bx, by) = verts[k], verts[(k + 1) % n]
+            area += ax * by - bx * ay
+        sgn = 1.0 if area > 0 else -1.0
+        for k in range(n):
+            (ax, ay), (bx, by) = verts[k], verts[(k + 1) % n]
+            inside &= sgn * ((bx - ax) * (sy - ay) - (by - ay) * (sx - ax)) >= 0
+        cov = inside.mean(axis=(2, 3))
+        img[y0:y1, x0:x1] = img[y0:y1, x0:x1] * (1 - cov) + val * cov
+    return img
+
+
+@dataclass
+class ContrastPair:
+    I: np.ndarray
+    J: np.ndarray
+    pts: np.ndarray  # float32 [n, 2] keypoints in I
+    gt: np.ndarray  # float64 [n, 2] positions of the keypoints under the scene motion
+    gain: float
+    seed: int
+
+
+def make_config3_contrast_pair(seed: int = 5, w: int = 1280, h: int = 1024, n_kp: int = 2000,
+                               n_rects: int = 900, gain: float = 1.3) -> ContrastPair:
+    """High-contrast variant of the precision workload: unblurred step edges
+    (rotated rectangles of grey levels 16-240 on a mid-grey background,
+    area-sampled), the second frame the same scene under a small rigid motion
+    (rotation up to 0.5 degrees, translation up to 5 px, sub-pixel) with
+    exposure x `gain` about mid-grey.  Step edges of contrast above 128 give
+    Scharr responses above 2048, where half-precision storage of raw/32
+    rounds the odd ones."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    polys = []
+    for _ in range(n_rects):
+        cx, cy = rng.uniform(-20, w + 20), rng.uniform(-20, h + 20)
+        a, b = rng.uniform(8, 40), rng.uniform(8, 40)
+        th = rng.uniform(0, np.pi)
+        c, s_ = np.cos(th), np.sin(th)
+        corners = np.array([[-a, -b], [a, -b], [a, b], [-a, b]]) @ np.array([[c, s_], [-s_, c]])
+        polys.append((corners + [cx, cy], float(rng.choice([rng.uniform(16, 70), rng.uniform(186, 240)]))))
+    theta = rng.uniform(-0.5, 0.5)
+    r, ang = rng.uniform(1.0, 5.0), rng.uniform(0, 2 * np.pi)
+    M = affine_from_motion(theta, r * np.cos(ang), r * np.sin(ang), (w - 1) / 2.0, (h - 1) / 2.0)
+    I = quantize_u8(_render_polygons(w, h, polys))
+    moved = [(v @ M[:, :2].T + M[:, 2], val) for v, val in polys]
+    J = quantize_u8((_render_polygons(w, h, moved) - 128.0) * gain + 128.0)
+    pts = select_keypoints_nms(I, n_kp, seed * 31 + 1, radius=4, margin=30.0)
+    gt = pts.astype(np.float64) @ M[:, :2].T + M[:, 2]
+    return ContrastPair(I, J, pts, gt, gain, seed)
 
 
 # ----------------------------------------------------------------- stream mix

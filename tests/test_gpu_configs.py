@@ -99,6 +99,57 @@ def test_precision_workload_fp16_gradients_error_stated(precision_seq):
     assert stats["mean"] < 0.005 and stats["p99"] < 0.02 and stats["max"] < 0.05, stats
 
 
+def half_rounded_fraction(pyr, pts, win=21, levels=1):
+    """Fraction of the gradient components in the (win + 1)^2 footprints of
+    the points' level-l templates (l < levels) whose half-precision storage
+    of raw/32 is inexact: an odd raw Scharr response above 2048 in
+    magnitude (half precision keeps 11 significant bits)."""
+    hw = win // 2
+    tot = rnd = 0
+    for l in range(levels):
+        gx, gy = pyr.gx[l].astype(np.int32), pyr.gy[l].astype(np.int32)
+        bad = ((np.abs(gx) > 2048) & (gx % 2 != 0)).astype(np.int32) + \
+            ((np.abs(gy) > 2048) & (gy % 2 != 0)).astype(np.int32)
+        h, w = gx.shape
+        for x, y in np.asarray(pts, np.float64) / 2 ** l:
+            x0, y0 = int(np.floor(x)) - hw, int(np.floor(y)) - hw
+            ys = np.clip(np.arange(y0, y0 + win + 1), 0, h - 1)
+            xs = np.clip(np.arange(x0, x0 + win + 1), 0, w - 1)
+            rnd += int(bad[np.ix_(ys, xs)].sum())
+            tot += 2 * len(ys) * len(xs)
+    return rnd / tot
+
+
+def test_precision_high_contrast_fp16_error_exercised():
+    """The precision configuration on a high-contrast variant (1280x1024,
+    2000 keypoints, unblurred step edges, exposure x1.3 on the second frame),
+    where odd Scharr responses above 2048 occur inside the windows, so FP16
+    gradient storage does round.  int16 storage meets full parity with the
+    FP64 oracle; FP16 storage's error against the oracle is stated (mean,
+    p99, max px, fraction of window samples rounded) and bounded, and it is
+    not zero: FP16 flows differ from int16 flows."""
+    import paper_2607_01757_gb300 as vt
+
+    c = synth.make_config3_contrast_pair(seed=5)
+    prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
+    r = _oracle_fb(c.I, c.J, c.pts, prm)
+    s_pts, s_st, _, s_rs = _gpu_fb(c.I, c.J, c.pts, prm, vt.VT_GRAD_S16)
+    st16 = compare(s_pts, s_st, s_rs, r, "high-contrast int16")
+    h_pts, h_st, _, _ = _gpu_fb(c.I, c.J, c.pts, prm, vt.VT_GRAD_F16)
+    both = (h_st == 1) & (r.status == 1)
+    d = np.hypot(*(h_pts[both] - r.fwd.pts[both]).T)
+    frac = half_rounded_fraction(oracle.build_pyramid(c.I, 5), c.pts, 21, 5)
+    stats = dict(mean=float(d.mean()), p99=float(np.percentile(d, 99)), max=float(d.max()),
+                 status_agree=float((h_st == r.status).mean()), tracked=int(both.sum()),
+                 rounded_samples=frac, int16=st16)
+    print("high-contrast fp16 gradients vs fp64 oracle:", stats)
+    assert frac > 1e-3, stats
+    changed = (h_st == 1) & (s_st == 1) & np.any(h_pts != s_pts, axis=1)
+    assert changed.sum() > 0, "FP16 storage changed no flow"
+    assert stats["status_agree"] >= 0.99, stats
+    assert stats["mean"] < 0.005 and stats["p99"] < 0.02 and stats["max"] < 0.05, stats
+
+
 @pytest.mark.parametrize("warps", [4, 8])
 def test_full_size_streams_batched_sampled(warps):
     """The batched launch of the benchmark on full-size stream shapes (one
@@ -185,3 +236,64 @@ def test_stereo_temporal_sequence_six_frames_batched():
             compare(out[0].cpu().numpy(), out[1].cpu().numpy(), out[3].cpu().numpy(), r, f"frame {t} {label}",
                     idx=idx)
     tr.free()
+
+
+def test_stereo_temporal_sequence_64_frames_pool_aging_batched():
+    """The stereo + temporal configuration as specified: 64 frames per
+    camera at 752x480 (camera rotation up to 5 degrees per frame, 0.3 m/s at
+    20 Hz), 1000 keypoints per frame, 5 levels, stepped frame by frame
+    through the batched engine.  The temporal task tracks a pool that ages:
+    the survivors of the previous step's forward-backward check keep being
+    tracked from their GPU positions, topped up with the previous frame's
+    new keypoints to 1000; the stereo task checks the current frame's
+    keypoints left->right.  At every frame both tasks agree with the oracle
+    on a seeded sample of 60 points each (the oracle tracks the same inputs)."""
+    import multiprocessing as mp
+    import os
+
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.engine import BatchedTracker
+
+    F, N = 64, 1000
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        seq = synth.make_stereo_sequence(seed=2, n_frames=F, w=752, h=480, n_kp=N, map_fn=pool.map)
+    spec = synth.StreamSpec(sid=0, w=752, h=480, stereo=True, n_kp=N, levels=5, seed=2)
+    prm = vt.KltParams(win=21, levels=5)
+    tr = BatchedTracker([spec], prm)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=a.dtype)).cuda()  # noqa: E731
+    rng = np.random.Generator(np.random.PCG64(64))
+    pool_pts = seq.kps[0].copy()
+    age = np.zeros(len(pool_pts), np.int64)
+    max_age, checked = 0, 0
+    for t in range(F):
+        L, R = dev(seq.left[t]), dev(seq.right[t])
+        n_t = len(pool_pts) if t > 0 else 0
+        kt = dev(pool_pts.astype(np.float32))
+        tr.stage(tr.step_tables([0], [n_t], [N], [L], [R], kpt=[kt], kps=[dev(seq.kps[t])]))
+        tr.run(graph=True)
+        tr.advance([0])
+        torch.cuda.synchronize()
+        s = tr.streams[0]
+        tasks = [(seq.left[t], seq.right[t], seq.kps[t], s.out_s, "stereo")]
+        if t > 0:
+            tasks.append((seq.left[t - 1], seq.left[t], pool_pts, s.out_t, "temporal"))
+        for I, J, kp, out, label in tasks:
+            n = len(kp)
+            idx = np.sort(rng.choice(n, size=60, replace=False))
+            r = _oracle_fb(I, J, kp[idx].astype(np.float32), prm)
+            compare(out[0][:n].cpu().numpy(), out[1][:n].cpu().numpy(), out[3][:n].cpu().numpy(), r,
+                    f"frame {t} {label}", idx=idx)
+            checked += 1
+        if t > 0:
+            ok = s.out_t[1][:n_t].cpu().numpy() == 1
+            surv = s.out_t[0][:n_t].cpu().numpy()[ok]
+            age = age[ok] + 1
+            fresh = seq.kps[t][:N - len(surv)]
+            pool_pts = np.concatenate([surv, fresh]).astype(np.float32)
+            age = np.concatenate([age, np.zeros(len(fresh), np.int64)])
+            max_age = max(max_age, int(age.max()))
+    tr.free()
+    assert checked == 2 * F - 1
+    assert max_age >= 20, max_age  # some tracks live through a third of the sequence

@@ -29,7 +29,7 @@ def test_served_mix_equals_alone_and_admission():
     trace = make_trace(specs, 8 * 4, seed=7, frames_per_stream=3)
     st = srv.serve(trace, realtime=False)
     assert st.served == len(trace) and st.batches >= 4 and st.mean_batch > 1.0
-    mixed = {i: (srv.h_out[i][0].clone(), srv.h_out[i][1].clone()) for i in range(len(specs))}
+    mixed = {i: tuple(t.clone() for t in srv.h_out[i]) for i in range(len(specs))}
     last = {}
     for r in trace:
         last[r.sid] = r
@@ -39,13 +39,16 @@ def test_served_mix_equals_alone_and_admission():
         solo = Server(specs, frames, prm, budget_bytes=1 << 34)
         reqs = [r for r in make_trace(specs, 8 * 4, seed=7, frames_per_stream=3) if r.sid == sid]
         solo.serve(reqs, realtime=False)
-        n = last[sid].n_features
-        assert n > 0
-        a_p, a_s = mixed[sid]
-        b_p, b_s = solo.h_out[sid]
-        assert np.array_equal(a_s[:n].numpy(), b_s[:n].numpy())
-        ok = a_s[:n].numpy().astype(bool)
-        assert np.array_equal(a_p[:n].numpy()[ok], b_p[:n].numpy()[ok])
+        counts = [last[sid].n_features, last[sid].n_stereo]
+        assert counts[0] > 0 and (counts[1] > 0) == specs[sid].stereo
+        # temporal results, then (stereo streams) the left->right results
+        for k in range(len(mixed[sid]) // 2):
+            n = counts[k]
+            a_p, a_s = mixed[sid][2 * k:2 * k + 2]
+            b_p, b_s = solo.h_out[sid][2 * k:2 * k + 2]
+            assert np.array_equal(a_s[:n].numpy(), b_s[:n].numpy())
+            ok = a_s[:n].numpy().astype(bool)
+            assert np.array_equal(a_p[:n].numpy()[ok], b_p[:n].numpy()[ok])
         solo.free()
 
 
