@@ -12,14 +12,15 @@
 //     g_{l-1} = 2 (g_l + nu)
 //   result v = u + g_0 + nu (bound test), error = mean |T - J_0(v + x)|.
 //
-// Mapping to the warp: lane c owns window column c for every row (lanes
-// c <= win load, lanes c < win compute).  Every window sample of one Newton
+// Mapping to the warp: the window is cut into short runs of rows of one
+// column, a lane owning one or two runs (KRuns), so all 32 lanes work on the
+// win^2 samples.  Every window sample of one Newton
 // iteration shares the same fractional bilinear weights (bx, by), so
 // b = sum (T - J(q + x)) grad T expands exactly into bx, by and eight moments
 // of the integer footprint of J under the window (cell_moments).  A sweep
 // over the footprint is needed only when the integer part of q changes;
 // iterations that stay in the same cell reuse the moments.  The template and
-// its gradients stay in registers (3 * win floats per lane); the image and
+// its gradients stay in registers (three floats per owned sample); the image and
 // gradient window it is sampled from, and each footprint, are staged in
 // per-warp shared memory by cp.async.  Sums over the window are per-lane FP32
 // sums over rows followed by a warp reduction that leaves bit-identical
@@ -170,11 +171,43 @@ struct KSmem {
     uint32_t g[(WIN + 1) * GS];
 };
 
-// Template of a level without stored gradients: lane c computes the raw
-// Scharr response of window column c from the level image itself -- the
-// integers the pyramid kernels would have stored (reflect-101 neighbours of
-// the replicate-clamped pixel) -- then samples exactly as load_template does,
-// so the result is bit-identical to tracking on stored int16 gradients.
+// Which window samples a lane owns.  The win x win window is cut into runs
+// of RL consecutive rows of one column (D runs per column, win * D runs in
+// all); lane l owns runs l, l + 32, ... (at most RPL).  A lane walks each of
+// its runs down the column, reading footprint rows r0 .. r0 + RL and the
+// neighbouring column from shared memory, so every lane works (with one
+// column per lane, 32 - win lanes would idle) and the right neighbour needs
+// no shuffle.  The per-sample arithmetic does not depend on the layout; only
+// the grouping of the per-lane partial sums does.
+template <int WIN>
+struct KRuns {
+    static constexpr int D = WIN == 31 ? 1 : 3;
+    static_assert(WIN % D == 0, "runs tile a column");
+    static constexpr int RL = WIN / D;          // samples per run
+    static constexpr int NR = WIN * D;          // runs in the window
+    static constexpr int RPL = (NR + 31) / 32;  // runs per lane
+    static constexpr int NS = RPL * RL;         // samples a lane holds
+};
+
+// Run i of a lane: column c, first row r0, and whether it lies in the window
+// (a lane's last run may not: it then reads run 0's addresses and its
+// samples weigh zero).
+template <int WIN>
+__device__ __forceinline__ void run_of(int lane, int i, int &c, int &r0, bool &valid) {
+    constexpr int D = KRuns<WIN>::D, RL = KRuns<WIN>::RL;
+    const int k = lane + 32 * i;
+    valid = k < KRuns<WIN>::NR;
+    const int kk = valid ? k : 0;
+    c = kk / D;
+    r0 = (kk - c * D) * RL;
+}
+
+// Gradient window of a level without stored gradients (VT_GRAD_NONE): lane c
+// (c <= win) computes the raw Scharr responses of staged column c -- the
+// integers the pyramid kernels would have stored for the replicate-clamped
+// pixel (reflect-101 neighbours) -- and stores them as int16 pairs in the
+// staged gradient window, with the pixel itself in the staged image window,
+// so the template is then sampled exactly as from stored int16 gradients.
 //
 // Per image row y the lane forms d(y) = I(y, x+1) - I(y, x-1) and
 // s(y) = 3 I(y, x-1) + 10 I(y, x) + 3 I(y, x+1); the gradient of row y is
@@ -184,17 +217,13 @@ struct KSmem {
 // image's first or last line takes its reflected neighbour (row 1 or h-2)
 // on both sides instead.
 template <int WIN>
-__device__ __forceinline__ void load_template_otf(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
-                                                  float (&GX)[WIN], float (&GY)[WIN]) {
-    constexpr int HW = WIN / 2;
-    const float fx = floorf(ux), fy = floorf(uy);
-    const float ax = ux - fx, ay = uy - fy;
-    const int x0 = (int)fx - HW, y0 = (int)fy - HW;
+__device__ __forceinline__ void stage_window_otf(const Level &L, int x0, int y0, int lane, KSmem<WIN> &sm) {
+    constexpr int JS = KSmem<WIN>::JS, GS = KSmem<WIN>::GS;
     const bool ld = lane <= WIN;
     const int q = clampi(x0 + lane, 0, L.w - 1);
     const int qm = refl101(q - 1, L.w), qp = refl101(q + 1, L.w);
     const int hm1 = L.h - 1;
-    auto terms = [&](int y, int &d, int &sm, int &c) {
+    auto terms = [&](int y, int &d, int &sm_, int &c) {
         const uint8_t *rp = L.img + (size_t)y * L.pitch;
         int a = 0, b = 0, e = 0;
         if (ld) {
@@ -203,7 +232,7 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
             e = __ldg(rp + qp);
         }
         d = e - a;
-        sm = 3 * (a + e) + 10 * b;
+        sm_ = 3 * (a + e) + 10 * b;
         c = b;
     };
     // reflected neighbours of the first and last image rows (used only when
@@ -214,125 +243,116 @@ __device__ __forceinline__ void load_template_otf(const Level &L, float ux, floa
     int dm, sm_m, cm, d0, s0, c0;
     terms(clampi(y0 - 1, 0, hm1), dm, sm_m, cm);
     terms(clampi(y0, 0, hm1), d0, s0, c0);
-    float pi = 0.f, pgx = 0.f, pgy = 0.f;
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r <= WIN; ++r) {
         const int yc = clampi(y0 + r, 0, hm1);
         int dp, sp, cp;
         terms(clampi(y0 + r + 1, 0, hm1), dp, sp, cp);
-        // first / last image row: the reflected neighbour on both sides
         const bool top = yc == 0, bot = yc == hm1;
         const int du = top ? dt : (bot ? db : dm), su = top ? st : (bot ? sb : sm_m);
         const int dd = top ? dt : (bot ? db : dp), sd = top ? st : (bot ? sb : sp);
-        const float gx = (float)(3 * (du + dd) + 10 * d0);
-        const float gy = (float)(sd - su);
-        const float mv = u8f((uint32_t)c0);
+        const int gx = 3 * (du + dd) + 10 * d0, gy = sd - su;
+        if (ld) {
+            sm.j[r * JS + lane] = (uint8_t)c0;
+            sm.g[r * GS + lane] = (uint32_t)(uint16_t)(int16_t)gx | ((uint32_t)(uint16_t)(int16_t)gy << 16);
+        }
         dm = d0;
         sm_m = s0;
         d0 = dp;
         s0 = sp;
         c0 = cp;
-        const float mvr = __shfl_down_sync(kFull, mv, 1);
-        const float gxr = __shfl_down_sync(kFull, gx, 1);
-        const float gyr = __shfl_down_sync(kFull, gy, 1);
-        const float hi = fmaf(ax, mvr - mv, mv);
-        const float hgx = fmaf(ax, gxr - gx, gx);
-        const float hgy = fmaf(ax, gyr - gy, gy);
-        if (r > 0) {
-            T[r - 1] = fmaf(ay, hi - pi, pi);
-            GX[r - 1] = fmaf(ay, hgx - pgx, pgx);
-            GY[r - 1] = fmaf(ay, hgy - pgy, pgy);
-        }
-        pi = hi;
-        pgx = hgx;
-        pgy = hgy;
     }
-    if (lane >= WIN) {
-#pragma unroll
-        for (int r = 0; r < WIN; ++r) T[r] = GX[r] = GY[r] = 0.f;
-    }
+    __syncwarp();
 }
 
-// Sample the template of level `L` around (ux, uy): lane c ends with column
-// c of T and of its gradients (zero for c >= WIN).  The (win + 1)^2 image and
-// gradient footprint is first staged in shared memory (16-byte cp.async
-// chunks of each clamped row when the columns lie inside the level -- they
-// may read up to 26 image bytes and 24 gradient bytes past a row's last
-// pixel, inside the pitch or the pyramid allocation's slack -- else one
-// clamped column per lane).
+// Sample the template of level `L` around (ux, uy) at the lane's window
+// samples (KRuns): T and its gradients, zero for samples outside the
+// window.  The (win + 1)^2 image and gradient footprint is first staged in
+// shared memory (16-byte cp.async chunks of each clamped row when the
+// columns lie inside the level -- they may read up to 26 image bytes and 24
+// gradient bytes past a row's last pixel, inside the pitch or the pyramid
+// allocation's slack -- else one clamped column per lane; computed in place
+// for a level without gradient planes).
 template <int WIN, int GT>
-__device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane, float (&T)[WIN],
-                                              float (&GX)[WIN], float (&GY)[WIN], KSmem<WIN> &sm) {
-    if constexpr (GT == VT_GRAD_NONE) {
-        load_template_otf<WIN>(L, ux, uy, lane, T, GX, GY);
-        return;
-    }
+__device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane,
+                                              float (&T)[KRuns<WIN>::NS], float (&GX)[KRuns<WIN>::NS],
+                                              float (&GY)[KRuns<WIN>::NS], KSmem<WIN> &sm) {
     constexpr int HW = WIN / 2;
     constexpr int NC = KSmem<WIN>::NC, JS = KSmem<WIN>::JS, NG = KSmem<WIN>::NG, GS = KSmem<WIN>::GS;
+    constexpr int RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
+    // staged gradient words are int16 pairs when computed in place
+    constexpr int GTS = GT == VT_GRAD_NONE ? VT_GRAD_S16 : GT;
     const float fx = floorf(ux), fy = floorf(uy);
     const float ax = ux - fx, ay = uy - fy;
     const int x0 = (int)fx - HW, y0 = (int)fy - HW;
     const int hm1 = L.h - 1;
     int offi, offg;
     __syncwarp();
-    if (x0 >= 0 && x0 + WIN < L.w) {
-        const int wx = x0 & ~15, gw = x0 & ~3;
-        offi = x0 - wx;
-        offg = x0 - gw;
-        const uint32_t sbj = (uint32_t)__cvta_generic_to_shared(sm.j);
-        const uint32_t sbg = (uint32_t)__cvta_generic_to_shared(sm.g);
-        for (int k = lane; k < (WIN + 1) * NC; k += 32) {
-            const int row = k / NC, c = k - row * NC;
-            const uint8_t *src = L.img + (size_t)clampi(y0 + row, 0, hm1) * L.pitch + wx + 16 * c;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbj + row * JS + 16 * c), "l"(src) : "memory");
-        }
-        for (int k = lane; k < (WIN + 1) * NG; k += 32) {
-            const int row = k / NG, c = k - row * NG;
-            const uint32_t *src = L.grad + (size_t)clampi(y0 + row, 0, hm1) * L.gpitch + gw + 4 * c;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbg + 4 * (row * GS + 4 * c)), "l"(src) : "memory");
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-    } else {
+    if constexpr (GT == VT_GRAD_NONE) {
         offi = offg = 0;
-        if (lane <= WIN) {
-            const int c = clampi(x0 + lane, 0, L.w - 1);
+        stage_window_otf<WIN>(L, x0, y0, lane, sm);
+    } else {
+        if (x0 >= 0 && x0 + WIN < L.w) {
+            const int wx = x0 & ~15, gw = x0 & ~3;
+            offi = x0 - wx;
+            offg = x0 - gw;
+            const uint32_t sbj = (uint32_t)__cvta_generic_to_shared(sm.j);
+            const uint32_t sbg = (uint32_t)__cvta_generic_to_shared(sm.g);
+            for (int k = lane; k < (WIN + 1) * NC; k += 32) {
+                const int row = k / NC, c = k - row * NC;
+                const uint8_t *src = L.img + (size_t)clampi(y0 + row, 0, hm1) * L.pitch + wx + 16 * c;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbj + row * JS + 16 * c), "l"(src)
+                             : "memory");
+            }
+            for (int k = lane; k < (WIN + 1) * NG; k += 32) {
+                const int row = k / NG, c = k - row * NG;
+                const uint32_t *src = L.grad + (size_t)clampi(y0 + row, 0, hm1) * L.gpitch + gw + 4 * c;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sbg + 4 * (row * GS + 4 * c)),
+                             "l"(src)
+                             : "memory");
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        } else {
+            offi = offg = 0;
+            if (lane <= WIN) {
+                const int c = clampi(x0 + lane, 0, L.w - 1);
 #pragma unroll
-            for (int r = 0; r <= WIN; ++r) {
-                const int row = clampi(y0 + r, 0, hm1);
-                sm.j[r * JS + lane] = __ldg(L.img + (size_t)row * L.pitch + c);
-                sm.g[r * GS + lane] = __ldg(L.grad + (size_t)row * L.gpitch + c);
+                for (int r = 0; r <= WIN; ++r) {
+                    const int row = clampi(y0 + r, 0, hm1);
+                    sm.j[r * JS + lane] = __ldg(L.img + (size_t)row * L.pitch + c);
+                    sm.g[r * GS + lane] = __ldg(L.grad + (size_t)row * L.gpitch + c);
+                }
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
-    const int cl = lane <= WIN ? lane : WIN;
-    const uint8_t *jr = &sm.j[offi + cl];
-    const uint32_t *gr = &sm.g[offg + cl];
-    float pi = 0.f, pgx = 0.f, pgy = 0.f;
 #pragma unroll
-    for (int r = 0; r <= WIN; ++r) {
-        const uint32_t v = jr[r * JS], g = gr[r * GS];
-        const float mv = u8f(v);
-        const float mvr = __shfl_down_sync(kFull, mv, 1);
-        float gx, gy;
-        unpack_grad<GT>(g, gx, gy);
-        const float gxr = __shfl_down_sync(kFull, gx, 1);
-        const float gyr = __shfl_down_sync(kFull, gy, 1);
-        const float hi = fmaf(ax, mvr - mv, mv);
-        const float hgx = fmaf(ax, gxr - gx, gx);
-        const float hgy = fmaf(ax, gyr - gy, gy);
-        if (r > 0) {
-            T[r - 1] = fmaf(ay, hi - pi, pi);
-            GX[r - 1] = fmaf(ay, hgx - pgx, pgx);
-            GY[r - 1] = fmaf(ay, hgy - pgy, pgy);
+    for (int i = 0; i < RPL; ++i) {
+        int c, r0;
+        bool valid;
+        run_of<WIN>(lane, i, c, r0, valid);
+        const uint8_t *jr = &sm.j[r0 * JS + offi + c];
+        const uint32_t *gr = &sm.g[r0 * GS + offg + c];
+        float pi = 0.f, pgx = 0.f, pgy = 0.f;
+#pragma unroll
+        for (int r = 0; r <= RL; ++r) {
+            const float mv = u8f(jr[r * JS]), mvr = u8f(jr[r * JS + 1]);
+            float gx, gy, gxr, gyr;
+            unpack_grad<GTS>(gr[r * GS], gx, gy);
+            unpack_grad<GTS>(gr[r * GS + 1], gxr, gyr);
+            const float hi = fmaf(ax, mvr - mv, mv);
+            const float hgx = fmaf(ax, gxr - gx, gx);
+            const float hgy = fmaf(ax, gyr - gy, gy);
+            if (r > 0) {
+                T[i * RL + r - 1] = valid ? fmaf(ay, hi - pi, pi) : 0.f;
+                GX[i * RL + r - 1] = valid ? fmaf(ay, hgx - pgx, pgx) : 0.f;
+                GY[i * RL + r - 1] = valid ? fmaf(ay, hgy - pgy, pgy) : 0.f;
+            }
+            pi = hi;
+            pgx = hgx;
+            pgy = hgy;
         }
-        pi = hi;
-        pgx = hgx;
-        pgy = hgy;
-    }
-    if (lane >= WIN) {
-#pragma unroll
-        for (int r = 0; r < WIN; ++r) T[r] = GX[r] = GY[r] = 0.f;
     }
 }
 
@@ -385,65 +405,77 @@ __device__ __forceinline__ int stage_footprint(const Level &L, int x0, int y0, i
 // The footprint differences are exact (integers); m[0..3] are the x parts
 // (R, Sx, Sy, Sxy against Tx), m[4..7] the y parts.
 template <int WIN>
-__device__ __forceinline__ void cell_moments(const Level &L, int x0, int y0, int lane, const float (&T)[WIN],
-                                             const float (&GX)[WIN], const float (&GY)[WIN], KSmem<WIN> &sm,
-                                             float (&m)[8]) {
-    constexpr int JS = KSmem<WIN>::JS;
+__device__ __forceinline__ void cell_moments(const Level &L, int x0, int y0, int lane,
+                                             const float (&T)[KRuns<WIN>::NS], const float (&GX)[KRuns<WIN>::NS],
+                                             const float (&GY)[KRuns<WIN>::NS], KSmem<WIN> &sm, float (&m)[8]) {
+    constexpr int JS = KSmem<WIN>::JS, RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
     const int off = stage_footprint<WIN>(L, x0, y0, lane, sm);
-    const uint8_t *jr = &sm.j[off + (lane <= WIN ? lane : WIN)];
     float a[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = 0.f;
-    float pmv = 0.f, pdx = 0.f;
 #pragma unroll
-    for (int r = 0; r <= WIN; ++r) {
-        const float mv = u8f(jr[r * JS]);
-        const float mvr = __shfl_down_sync(kFull, mv, 1);
-        const float dx = mvr - mv;  // F(r, c+1) - F(r, c), exact
-        if (r > 0) {
-            const float e0 = T[r - 1] - pmv;
-            const float sy = mv - pmv;   // F10 - F00
-            const float sxy = dx - pdx;  // F11 - F10 - F01 + F00
-            const float gx = GX[r - 1], gy = GY[r - 1];
-            a[0] = fmaf(e0, gx, a[0]);
-            a[1] = fmaf(pdx, gx, a[1]);
-            a[2] = fmaf(sy, gx, a[2]);
-            a[3] = fmaf(sxy, gx, a[3]);
-            a[4] = fmaf(e0, gy, a[4]);
-            a[5] = fmaf(pdx, gy, a[5]);
-            a[6] = fmaf(sy, gy, a[6]);
-            a[7] = fmaf(sxy, gy, a[7]);
+    for (int i = 0; i < RPL; ++i) {
+        int c, r0;
+        bool valid;
+        run_of<WIN>(lane, i, c, r0, valid);  // samples of a run outside the window weigh zero
+        const uint8_t *jr = &sm.j[r0 * JS + off + c];
+        float pmv = 0.f, pdx = 0.f;
+#pragma unroll
+        for (int r = 0; r <= RL; ++r) {
+            const float mv = u8f(jr[r * JS]);
+            const float dx = u8f(jr[r * JS + 1]) - mv;  // F(r, c+1) - F(r, c), exact
+            if (r > 0) {
+                const int s = i * RL + r - 1;
+                const float e0 = T[s] - pmv;
+                const float sy = mv - pmv;   // F10 - F00
+                const float sxy = dx - pdx;  // F11 - F10 - F01 + F00
+                const float gx = GX[s], gy = GY[s];
+                a[0] = fmaf(e0, gx, a[0]);
+                a[1] = fmaf(pdx, gx, a[1]);
+                a[2] = fmaf(sy, gx, a[2]);
+                a[3] = fmaf(sxy, gx, a[3]);
+                a[4] = fmaf(e0, gy, a[4]);
+                a[5] = fmaf(pdx, gy, a[5]);
+                a[6] = fmaf(sy, gy, a[6]);
+                a[7] = fmaf(sxy, gy, a[7]);
+            }
+            pmv = mv;
+            pdx = dx;
         }
-        pmv = mv;
-        pdx = dx;
     }
     warp_sum8(a, lane, m);
 }
 
 // Error sweep at (qx, qy): sum |T - J_l(q + x)| over the window.
 template <int WIN>
-__device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy, int lane, const float (&T)[WIN],
-                                              KSmem<WIN> &sm) {
-    constexpr int HW = WIN / 2, JS = KSmem<WIN>::JS;
+__device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy, int lane,
+                                              const float (&T)[KRuns<WIN>::NS], KSmem<WIN> &sm) {
+    constexpr int HW = WIN / 2, JS = KSmem<WIN>::JS, RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
     const float fx = floorf(qx), fy = floorf(qy);
     const float bx = qx - fx, by = qy - fy;
     const int off = stage_footprint<WIN>(L, (int)fx - HW, (int)fy - HW, lane, sm);
-    const uint8_t *jr = &sm.j[off + (lane <= WIN ? lane : WIN)];
-    float sa = 0.f, sb = 0.f, ph = 0.f;
+    float sa = 0.f, sb = 0.f;
 #pragma unroll
-    for (int r = 0; r <= WIN; ++r) {
-        const float mv = u8f(jr[r * JS]);
-        const float mvr = __shfl_down_sync(kFull, mv, 1);
-        const float h = fmaf(bx, mvr - mv, mv);
-        if (r > 0) {
-            const float jv = fmaf(by, h - ph, ph);
-            const float e = (lane < WIN) ? fabsf(T[r - 1] - jv) : 0.f;
-            if (r & 1)
-                sa += e;
-            else
-                sb += e;
+    for (int i = 0; i < RPL; ++i) {
+        int c, r0;
+        bool valid;
+        run_of<WIN>(lane, i, c, r0, valid);
+        const uint8_t *jr = &sm.j[r0 * JS + off + c];
+        float ph = 0.f;
+#pragma unroll
+        for (int r = 0; r <= RL; ++r) {
+            const float mv = u8f(jr[r * JS]);
+            const float h = fmaf(bx, u8f(jr[r * JS + 1]) - mv, mv);
+            if (r > 0) {
+                const float jv = fmaf(by, h - ph, ph);
+                const float e = valid ? fabsf(T[i * RL + r - 1] - jv) : 0.f;
+                if (r & 1)
+                    sa += e;
+                else
+                    sb += e;
+            }
+            ph = h;
         }
-        ph = h;
     }
     return warp_sum(sa + sb);
 }
@@ -458,7 +490,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     constexpr float unit = grad_unit<GT>();
     // lambda_min normalisation: stored units^2 -> (grey/px)^2, / (N 255^2)
     const float inv_norm = unit * unit / (N * 65025.0f);
-    float T[WIN], GX[WIN], GY[WIN];
+    constexpr int NS = KRuns<WIN>::NS;
+    float T[NS], GX[NS], GY[NS];
     const int L = P.levels;
     float gx = 0.f, gy = 0.f, nux = 0.f, nuy = 0.f;
     int lost_level = 0;
@@ -492,7 +525,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         ++o.tmpl;
         float a11 = 0.f, a12 = 0.f, a22 = 0.f;
 #pragma unroll
-        for (int r = 0; r < WIN; ++r) {
+        for (int r = 0; r < NS; ++r) {
             a11 = fmaf(GX[r], GX[r], a11);
             a12 = fmaf(GX[r], GY[r], a12);
             a22 = fmaf(GY[r], GY[r], a22);
