@@ -172,8 +172,10 @@ struct KSmem {
 };
 
 // Which window samples a lane owns.  The win x win window is cut into runs
-// of RL consecutive rows of one column (D runs per column, win * D runs in
-// all); lane l owns runs l, l + 32, ... (at most RPL).  A lane walks each of
+// of RL consecutive rows of one column (D bands of RL rows, win * D runs in
+// all, numbered band by band so that lanes reading at the same time touch at
+// most two staged rows: fewer shared-memory bank conflicts); lane l owns
+// runs l, l + 32, ... (at most RPL).  A lane walks each of
 // its runs down the column, reading footprint rows r0 .. r0 + RL and the
 // neighbouring column from shared memory, so every lane works (with one
 // column per lane, 32 - win lanes would idle) and the right neighbour needs
@@ -194,12 +196,13 @@ struct KRuns {
 // samples weigh zero).
 template <int WIN>
 __device__ __forceinline__ void run_of(int lane, int i, int &c, int &r0, bool &valid) {
-    constexpr int D = KRuns<WIN>::D, RL = KRuns<WIN>::RL;
+    constexpr int RL = KRuns<WIN>::RL;
     const int k = lane + 32 * i;
     valid = k < KRuns<WIN>::NR;
     const int kk = valid ? k : 0;
-    c = kk / D;
-    r0 = (kk - c * D) * RL;
+    const int band = kk / WIN;
+    c = kk - band * WIN;
+    r0 = band * RL;
 }
 
 // Gradient window of a level without stored gradients (VT_GRAD_NONE): lane c

@@ -78,6 +78,31 @@ __device__ __forceinline__ void stage_tile(uint8_t (*s)[IW], const uint8_t *src,
     }
 }
 
+// stage_tile without waiting: an interior tile is copied by 16-byte
+// cp.async chunks (global to shared, L1 bypassed) that complete at the
+// caller's cp.async wait; a border tile (reflect-101 mapping) or an
+// unaligned source is staged byte by byte with plain loads and stores.
+template <int IH, int IW>
+__device__ __forceinline__ void stage_tile_async(uint8_t (*s)[IW], const uint8_t *src, int w, int h, int pitch,
+                                                 int ix0, int iy0, bool vec_ok) {
+    const bool interior = vec_ok && ix0 >= 0 && ix0 + IW <= w && iy0 >= 0 && iy0 + IH <= h;
+    if (interior) {
+        constexpr int C16 = IW / 16;
+        const uint32_t sb = (uint32_t)__cvta_generic_to_shared(&s[0][0]);
+        for (int i = threadIdx.x; i < IH * C16; i += blockDim.x) {
+            const int r = i / C16, c = i - r * C16;
+            const uint8_t *g = src + (size_t)(iy0 + r) * pitch + ix0 + 16 * c;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + r * IW + 16 * c), "l"(g) : "memory");
+        }
+    } else {
+        for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
+            const int r = i / IW, c = i - r * IW;
+            const int sy = refl101(iy0 + r, h), sx = refl101(ix0 + c, w);
+            s[r][c] = __ldg(src + (size_t)sy * pitch + sx);
+        }
+    }
+}
+
 // Copy the staged rows [r0, r0 + nr) x staged columns [c0, c0 + 128) to
 // dst rows y0.. / columns x0.. (x0 a multiple of 128, dst rows 16-byte aligned).
 template <int IW>
@@ -319,9 +344,16 @@ struct PyrTileRef {
     int ix0, iy0;
 };
 
+// Resident CTAs per SM the batched pyramid kernel is register-budgeted for.
+constexpr int PD_MIN_BLOCKS = 5;
+
+// Tiles are software-pipelined: while a CTA computes tile t from one staging
+// buffer, the copies of its next tile (t + gridDim.x) into the other buffer
+// are in flight, so the global-load latency overlaps the vertical, Scharr and
+// horizontal passes instead of stalling the CTA at every tile.
 template <int GT>
-__global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l) {
-    __shared__ __align__(16) uint8_t s_in[PD_IH][PD_IW];
+__global__ void __launch_bounds__(PD_THREADS, PD_MIN_BLOCKS) k_pyr_batch(const uint8_t *tab, int l) {
+    __shared__ __align__(16) uint8_t s_in[2][PD_IH][PD_IW];
     __shared__ uint16_t s_v[PD_TH][PD_VW];
     __shared__ BLvlJob s_jobs[kJobsInSmem];
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
@@ -351,15 +383,35 @@ __global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, in
         r.ix0 = 2 * tx * PD_TW - 16;
         r.iy0 = 2 * ty * PD_TH - 2;
     };
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    auto issue = [&](int t, int buf) {
+        PyrTileRef r;
+        BFrame fr;
+        int tx, ty;
+        locate(t, r, fr, tx, ty);
+        stage_tile_async<PD_IH, PD_IW>(s_in[buf], r.src, r.w, r.h, r.pitch, r.ix0, r.iy0, r.vec_ok);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    issue(blockIdx.x, 0);
+    int buf = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, buf ^= 1) {
+        const int tn = t + gridDim.x;
+        if (tn < tiles)
+            issue(tn, buf ^ 1);
+        else
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // tile t's copies (this thread's) landed
+        __syncthreads();                                         // everyone's
         PyrTileRef r;
         BFrame fr;
         int tx, ty;
         locate(t, r, fr, tx, ty);
         const Level src = fr.lv[l], dst = fr.lv[l + 1];
-        pyr_tile<GT != VT_GRAD_NONE, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad,
-                                         src.gpitch, l == 0 ? src.img : nullptr, src.pitch, tx, ty, s_in, s_v);
-        __syncthreads();
+        // level 0 also writes the pyramid's own level-0 copy, unless the
+        // frame was built in place (the caller's image is that level)
+        uint8_t *copy = (l == 0 && r.src != src.img) ? src.img : nullptr;
+        pyr_tile_compute<GT != VT_GRAD_NONE, GT>(src.w, src.h, dst.img, dst.pitch, src.grad, src.gpitch, copy,
+                                                 src.pitch, tx, ty, s_in[buf], s_v);
+        __syncthreads();  // s_in[buf] and s_v are free again
     }
 }
 
@@ -479,7 +531,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
                     for (int x = lane; x < Lc.w; x += 32) {
                         const uint8_t v = sr[x];
                         cur[y * Lc.pitch + x] = v;
-                        if (part == 0) Lc.img[(size_t)y * Lc.pitch + x] = v;
+                        if (part == 0 && src != Lc.img) Lc.img[(size_t)y * Lc.pitch + x] = v;
                     }
                 }
             }
@@ -508,9 +560,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
                 for (int t = 0; t < tiles; ++t) {
                     const int ty = t / tiles_x, tx = t - ty * tiles_x;
                     scharr_tile<GT>(src, Lc.w, Lc.h, sp, c == 0 ? fr.vec_ok != 0 : true, Lc.grad, Lc.gpitch,
-                                    c == 0 ? Lc.img : nullptr, Lc.pitch, tx, ty, s_in);
+                                    (c == 0 && src != Lc.img) ? Lc.img : nullptr, Lc.pitch, tx, ty, s_in);
                 }
-            } else if (c == 0) {  // no gradients: only the level-0 copy of a large one-level pyramid
+            } else if (c == 0 && src != Lc.img) {  // no gradients: only the level-0 copy of a large one-level pyramid
                 const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
                 for (int y = threadIdx.x >> 5; y < Lc.h; y += nw)
                     for (int x = lane; x < Lc.w; x += 32) Lc.img[(size_t)y * Lc.pitch + x] = src[(size_t)y * sp + x];
