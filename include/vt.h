@@ -126,6 +126,18 @@ VT_API vt_status vt_pyramid_build_grad(const uint8_t *img, int w, int h, int pit
  */
 VT_API vt_status vt_pyramid_create(int w, int h, int levels, vt_pyramid **out);
 
+/*
+ * vt_pyramid_upload - copy a w x h frame (`pitch` bytes per row; host memory,
+ * pinned for an asynchronous copy, or device memory with img_on_device = 1)
+ * into level 0 of `p` on `cuda_stream` (one 2-D memory copy, no kernel), so
+ * that a later build names level 0 itself as its image and copies nothing.
+ * The caller must not upload into a pyramid that queued work still reads.
+ * VT_ERR_ARG for a null pointer or pitch < w; VT_ERR_CUDA if the copy fails
+ * to start.
+ */
+VT_API vt_status vt_pyramid_upload(vt_pyramid *p, const uint8_t *img, int pitch, int img_on_device,
+                                   void *cuda_stream);
+
 /* Level `lvl` of `p`: device image pointer, size and pitch (bytes). */
 VT_API vt_status vt_pyramid_level(const vt_pyramid *p, int lvl, const uint8_t **ptr, int *w, int *h, int *pitch);
 
@@ -398,7 +410,10 @@ VT_API vt_status vt_tracks_spawn(const vt_spawn_job *jobs, int njobs, void *cuda
 /* Build pyramid `pyr` (levels and gradients) from the device image `img`
  * (the pyramid's w x h, `pitch` bytes per row, any alignment; pinned host
  * memory also works -- the kernels then read it over the host link, which is
- * slower than copying it first). */
+ * slower than copying it first).  `img` may be the pyramid's own level 0
+ * (vt_pyramid_level(pyr, 0, ...), with that level's pitch; VT_ERR_ARG with
+ * another pitch), for instance after vt_pyramid_upload: the frame is then
+ * built in place and level 0 is not copied. */
 typedef struct vt_frame_job {
     const uint8_t *img;
     int pitch;

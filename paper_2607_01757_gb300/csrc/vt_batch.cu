@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARP
     const int total = H->total_points, nt = H->ntasks;
     const KParams P = H->P;
     const int lane = threadIdx.x & 31;
+    pdl_wait();  // the pyramids are the previous launch's output
     for (;;) {
         int p = 0;
         if (lane == 0) p = atomicAdd(counter, 1);
@@ -183,9 +184,12 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
     const KltBatchKernel kb = klt_batch_kernel(tp.win, tp.gtype, tp.klt_warps);
     if (!kb.fn) return VT_ERR_ARG;
     if (ev && ev[2]) cudaEventRecord(ev[2], s);
-    kb.fn<<<tp.klt_grid, tp.klt_warps * 32, kb.smem, s>>>(b->dev[k], b->counter + k);
+    // starts while the last pyramid launch finishes (programmatic dependent
+    // launch), unless events are recorded for per-launch timing
+    const cudaError_t e =
+        launch_pdl(kb.fn, tp.klt_grid, tp.klt_warps * 32, kb.smem, s, !ev, (const uint8_t *)b->dev[k], b->counter + k);
     if (ev && ev[3]) cudaEventRecord(ev[3], s);
-    if (cudaGetLastError() != cudaSuccess) return VT_ERR_CUDA;
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VT_ERR_CUDA;
     if (tp.gate) return launch_gate_batch(b->dev[k], b->gate_grid, s);
     return VT_OK;
 }
@@ -265,6 +269,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     for (int f = 0; f < nframes; ++f) {
         const vt_frame_job &fj = frames[f];
         if (!fj.img || !fj.pyr || fj.pitch < fj.pyr->w) return VT_ERR_ARG;
+        if (fj.img == fj.pyr->lv[0].img && fj.pitch != fj.pyr->lv[0].pitch) return VT_ERR_ARG;  // in place
         for (int g = 0; g < f; ++g)
             if (frames[g].pyr == fj.pyr) return VT_ERR_ARG;  // one build per pyramid per run
     }

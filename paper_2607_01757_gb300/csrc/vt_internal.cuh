@@ -50,6 +50,35 @@ __device__ __forceinline__ int refl101(int i, int n) {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation (launch_pdl) may start before the previous kernel on its
+// stream has finished: it reads only what was ready before that kernel began
+// (job tables) until pdl_wait() returns, which happens once the previous
+// kernel has completed and its writes are visible.  pdl_trigger() lets the
+// next such kernel start launching (its CTAs fill the SMs this kernel's
+// finished CTAs leave).  Both are no-ops for a normally launched kernel.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// Launch `k` on stream `s`, with programmatic stream serialisation when
+// `pdl` (the kernel must call pdl_wait() before it reads the previous
+// kernel's output).
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(Params...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------- pyramid jobs
 // A pyrDown (and optionally Scharr) job: level src (w x h) -> dst
 // (ceil(w/2) x ceil(h/2)); gradients of the src level when grad != nullptr.

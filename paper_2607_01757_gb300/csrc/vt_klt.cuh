@@ -169,6 +169,7 @@ struct KSmem {
     static_assert(GS >= 3 + WIN + 1 && 4 * (GS - WIN - 1) <= 32, "a staged gradient row covers the window row "
                                                                  "and reads at most 32 bytes past it");
     uint32_t g[(WIN + 1) * GS];
+    uint8_t t[(WIN + 1) * JS];  // the template's image window, kept while footprints are staged (FP64 levels)
 };
 
 // Which window samples a lane owns.  The win x win window is cut into runs
@@ -280,7 +281,7 @@ __device__ __forceinline__ void stage_window_otf(const Level &L, int x0, int y0,
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane,
                                               float (&T)[KRuns<WIN>::NS], float (&GX)[KRuns<WIN>::NS],
-                                              float (&GY)[KRuns<WIN>::NS], KSmem<WIN> &sm) {
+                                              float (&GY)[KRuns<WIN>::NS], KSmem<WIN> &sm, int &offi, int &offg) {
     constexpr int HW = WIN / 2;
     constexpr int NC = KSmem<WIN>::NC, JS = KSmem<WIN>::JS, NG = KSmem<WIN>::NG, GS = KSmem<WIN>::GS;
     constexpr int RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
@@ -290,7 +291,6 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
     const float ax = ux - fx, ay = uy - fy;
     const int x0 = (int)fx - HW, y0 = (int)fy - HW;
     const int hm1 = L.h - 1;
-    int offi, offg;
     __syncwarp();
     if constexpr (GT == VT_GRAD_NONE) {
         offi = offg = 0;
@@ -483,6 +483,209 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
     return warp_sum(sa + sb);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 levels.  Where the gradient matrix of a level's template is
+// ill-conditioned (lambda_max / lambda_min above kFp64Cond), the FP32 sums of
+// G and b lose the weak direction: their rounding, divided by lambda_min,
+// moves the Newton steps along it by more than the flow tolerance.  Such a
+// level is tracked in FP64: the template and its gradients are sampled in
+// FP64 from the staged windows (kept in sm.t / sm.g) at every sweep, G, the
+// footprint moments, the 2x2 solve and the position update are FP64.  The
+// branch is warp-uniform; with the default eigenvalue threshold (1e-4) a
+// 21 x 21 window cannot exceed a condition number of about 5e3, so it is
+// taken only when a caller lowers the threshold.
+constexpr float kFp64Cond = 1e4f;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+// Keep the template's image window: copy sm.j (as staged by load_template)
+// to sm.t before footprints overwrite it.
+template <int WIN>
+__device__ __forceinline__ void keep_template_window(int lane, KSmem<WIN> &sm) {
+    constexpr int NB = (WIN + 1) * KSmem<WIN>::JS / 16;
+    __syncwarp();
+    const uint4 *src = reinterpret_cast<const uint4 *>(sm.j);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.t);
+    for (int k = lane; k < NB; k += 32) dst[k] = src[k];
+    __syncwarp();
+}
+
+// The lane's samples of one staged template row pair in FP64: horizontal
+// lerps of row r of the template image and gradient windows.
+template <int WIN, int GT>
+__device__ __forceinline__ void tmpl_row64(const uint8_t *tr, const uint32_t *gr, int r, double ax, double unit,
+                                           double &hT, double &hGX, double &hGY) {
+    constexpr int JS = KSmem<WIN>::JS, GS = KSmem<WIN>::GS;
+    constexpr int GTS = GT == VT_GRAD_NONE ? VT_GRAD_S16 : GT;
+    const double t0 = (double)tr[r * JS], t1 = (double)tr[r * JS + 1];
+    float gx0, gy0, gx1, gy1;
+    unpack_grad<GTS>(gr[r * GS], gx0, gy0);
+    unpack_grad<GTS>(gr[r * GS + 1], gx1, gy1);
+    const double x0 = (double)gx0 * unit, x1 = (double)gx1 * unit, y0 = (double)gy0 * unit, y1 = (double)gy1 * unit;
+    hT = fma(ax, t1 - t0, t0);
+    hGX = fma(ax, x1 - x0, x0);
+    hGY = fma(ax, y1 - y0, y0);
+}
+
+// G of the level's template in FP64 (grey levels per pixel), every lane
+// holding the totals.
+template <int WIN, int GT>
+__device__ __forceinline__ void template_G64(double ax, double ay, int offi, int offg, int lane, const KSmem<WIN> &sm,
+                                             double &g11, double &g12, double &g22) {
+    constexpr int JS = KSmem<WIN>::JS, GS = KSmem<WIN>::GS, RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
+    constexpr double unit = (double)grad_unit<GT>();
+    double a11 = 0.0, a12 = 0.0, a22 = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < RPL; ++i) {
+        int c, r0;
+        bool valid;
+        run_of<WIN>(lane, i, c, r0, valid);
+        if (!valid) continue;
+        const uint8_t *tr = &sm.t[r0 * JS + offi + c];
+        const uint32_t *gr = &sm.g[r0 * GS + offg + c];
+        double pT, pX, pY;
+        tmpl_row64<WIN, GT>(tr, gr, 0, ax, unit, pT, pX, pY);
+#pragma unroll 1
+        for (int r = 1; r <= RL; ++r) {
+            double hT, hX, hY;
+            tmpl_row64<WIN, GT>(tr, gr, r, ax, unit, hT, hX, hY);
+            const double gx = fma(ay, hX - pX, pX), gy = fma(ay, hY - pY, pY);
+            a11 = fma(gx, gx, a11);
+            a12 = fma(gx, gy, a12);
+            a22 = fma(gy, gy, a22);
+            pT = hT;
+            pX = hX;
+            pY = hY;
+        }
+    }
+    g11 = warp_sum_d(a11);
+    g12 = warp_sum_d(a12);
+    g22 = warp_sum_d(a22);
+}
+
+// The eight footprint moments of cell_moments in FP64, the template sampled
+// in FP64 from the kept windows (grey levels per pixel).
+template <int WIN, int GT>
+__device__ __forceinline__ void cell_moments64(const Level &L, int x0, int y0, double ax, double ay, int offi,
+                                               int offg, int lane, KSmem<WIN> &sm, double (&m)[8]) {
+    constexpr int JS = KSmem<WIN>::JS, GS = KSmem<WIN>::GS, RL = KRuns<WIN>::RL, RPL = KRuns<WIN>::RPL;
+    constexpr double unit = (double)grad_unit<GT>();
+    const int off = stage_footprint<WIN>(L, x0, y0, lane, sm);
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < RPL; ++i) {
+        int c, r0;
+        bool valid;
+        run_of<WIN>(lane, i, c, r0, valid);
+        if (!valid) continue;
+        const uint8_t *tr = &sm.t[r0 * JS + offi + c];
+        const uint32_t *gr = &sm.g[r0 * GS + offg + c];
+        const uint8_t *jr = &sm.j[r0 * JS + off + c];
+        double pT, pX, pY;
+        tmpl_row64<WIN, GT>(tr, gr, 0, ax, unit, pT, pX, pY);
+        double pmv = (double)jr[0];
+        double pdx = (double)jr[1] - pmv;
+#pragma unroll 1
+        for (int r = 1; r <= RL; ++r) {
+            double hT, hX, hY;
+            tmpl_row64<WIN, GT>(tr, gr, r, ax, unit, hT, hX, hY);
+            const double T = fma(ay, hT - pT, pT), gx = fma(ay, hX - pX, pX), gy = fma(ay, hY - pY, pY);
+            const double mv = (double)jr[r * JS];
+            const double dx = (double)jr[r * JS + 1] - mv;
+            const double e0 = T - pmv, sy = mv - pmv, sxy = dx - pdx;
+            a[0] = fma(e0, gx, a[0]);
+            a[1] = fma(pdx, gx, a[1]);
+            a[2] = fma(sy, gx, a[2]);
+            a[3] = fma(sxy, gx, a[3]);
+            a[4] = fma(e0, gy, a[4]);
+            a[5] = fma(pdx, gy, a[5]);
+            a[6] = fma(sy, gy, a[6]);
+            a[7] = fma(sxy, gy, a[7]);
+            pT = hT;
+            pX = hX;
+            pY = hY;
+            pmv = mv;
+            pdx = dx;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = warp_sum_d(a[k]);
+}
+
+// Result of one FP64 level.
+struct Level64 {
+    double nx, ny;  // step sum from the level's guess
+    float lmin;     // normalised lambda_min (FP64, rounded)
+    int reason;     // VT_TRACKED, VT_LOST_EIG or VT_LOST_OOB
+    int iters, sweeps;
+};
+
+// One level in FP64 (see kFp64Cond): the eigenvalue test and the Newton
+// iterations from the level's guess (gx, gy).  Kept out of line, with its
+// arguments and result passed by value, so that its FP64 registers do not
+// weigh on the FP32 path.
+template <int WIN, int GT>
+__device__ __noinline__ Level64 track_level64(const Level Jl, const int max_iters, const float eps2,
+                                              const float min_eig, float ux, float uy, float gx, float gy, int offi,
+                                              int offg, int lane, KSmem<WIN> *smp) {
+    constexpr int HW = WIN / 2;
+    constexpr double N = (double)(WIN * WIN);
+    KSmem<WIN> &sm = *smp;
+    Level64 o;
+    o.reason = VT_TRACKED;
+    o.iters = 0;
+    o.sweeps = 0;
+    o.nx = o.ny = 0.0;
+    keep_template_window<WIN>(lane, sm);
+    const double ax = (double)(ux - floorf(ux)), ay = (double)(uy - floorf(uy));
+    double G11, G12, G22;
+    template_G64<WIN, GT>(ax, ay, offi, offg, lane, sm, G11, G12, G22);
+    const double det64 = G11 * G22 - G12 * G12;
+    const double lmax64 = 0.5 * (G11 + G22 + sqrt((G11 - G22) * (G11 - G22) + 4.0 * G12 * G12));
+    const double lmin64 = det64 / lmax64 / (N * 65025.0);
+    o.lmin = (float)lmin64;
+    if (!(lmin64 >= (double)min_eig) || !(det64 > 0.0)) {
+        o.reason = VT_LOST_EIG;
+        return o;
+    }
+    int cx = INT_MIN, cy = INT_MIN;
+    double m[8];
+    const double uxd = (double)ux + (double)gx, uyd = (double)uy + (double)gy;
+    for (int k = 0; k < max_iters; ++k) {
+        const double qx = uxd + o.nx, qy = uyd + o.ny;
+        const double dist = fmin(fmin(qx + (double)HW, (double)(Jl.w - 1 + HW) - qx),
+                                 fmin(qy + (double)HW, (double)(Jl.h - 1 + HW) - qy));
+        if (!(dist >= 0.0)) {
+            o.reason = VT_LOST_OOB;
+            return o;
+        }
+        const double fx = floor(qx), fy = floor(qy);
+        const int ix = (int)fx - HW, iy = (int)fy - HW;
+        if (ix != cx || iy != cy) {
+            cell_moments64<WIN, GT>(Jl, ix, iy, ax, ay, offi, offg, lane, sm, m);
+            cx = ix;
+            cy = iy;
+            ++o.sweeps;
+        }
+        const double bx = qx - fx, by = qy - fy, bxy = bx * by;
+        const double b1 = m[0] - bx * m[1] - by * m[2] - bxy * m[3];
+        const double b2 = m[4] - bx * m[5] - by * m[6] - bxy * m[7];
+        const double ex = (G22 * b1 - G12 * b2) / det64;
+        const double ey = (G11 * b2 - G12 * b1) / det64;
+        o.nx += ex;
+        o.ny += ey;
+        ++o.iters;
+        if (ex * ex + ey * ey < (double)eps2) break;
+    }
+    return o;
+}
+
 // Track one point u = (ux0, uy0) from pyramid I to pyramid J.
 template <int WIN, int GT>
 __device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
@@ -497,6 +700,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     float T[NS], GX[NS], GY[NS];
     const int L = P.levels;
     float gx = 0.f, gy = 0.f, nux = 0.f, nuy = 0.f;
+    double nx64 = 0.0, ny64 = 0.0;  // the step sum of an FP64 level
+    bool level64 = false;           // the last level examined ran in FP64
     int lost_level = 0;
     o.status = 1;
     o.reason = VT_TRACKED;
@@ -524,7 +729,8 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         const Level Jl = J[l];
         const float s = pow2neg(l);
         const float ux = ux0 * s, uy = uy0 * s;
-        load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY, sm);
+        int offi, offg;
+        load_template<WIN, GT>(Il, ux, uy, lane, T, GX, GY, sm, offi, offg);
         ++o.tmpl;
         float a11 = 0.f, a12 = 0.f, a22 = 0.f;
 #pragma unroll
@@ -542,6 +748,28 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         const float lmin = det / lmax;
         o.lmin = lmin * inv_norm;
         nux = nuy = 0.f;
+        level64 = !(lmin * kFp64Cond >= lmax);  // ill-conditioned (or det <= 0): decide and track in FP64
+        if (level64) {
+            const Level64 r = track_level64<WIN, GT>(Jl, P.max_iters, P.eps2, P.min_eig, ux, uy, gx, gy, offi, offg,
+                                                     lane, &sm);
+            o.lmin = r.lmin;
+            o.iters += r.iters;
+            o.sweeps += r.sweeps;
+            nx64 = r.nx;
+            ny64 = r.ny;
+            if (r.reason != VT_TRACKED) {
+                o.status = 0;
+                o.reason = r.reason;
+                lost_level = l;
+                break;
+            }
+            if (l > 0) {
+                gx = (float)(2.0 * ((double)gx + nx64));
+                gy = (float)(2.0 * ((double)gy + ny64));
+                level64 = false;
+            }
+            continue;
+        }
         if (!(o.lmin >= P.min_eig) || !(det > 0.f)) {
             o.status = 0;
             o.reason = VT_LOST_EIG;
@@ -595,8 +823,13 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     {
         const float sc = (float)(1 << lost_level);
         const float si = pow2neg(lost_level);
-        o.x = (ux0 * si + gx + nux) * sc;
-        o.y = (uy0 * si + gy + nuy) * sc;
+        if (level64) {
+            o.x = (float)(((double)(ux0 * si) + (double)gx + nx64) * (double)sc);
+            o.y = (float)(((double)(uy0 * si) + (double)gy + ny64) * (double)sc);
+        } else {
+            o.x = (ux0 * si + gx + nux) * sc;
+            o.y = (uy0 * si + gy + nuy) * sc;
+        }
     }
     if (o.status) {
         const float dist = fminf(fminf(o.x, (float)(I[0].w - 1) - o.x), fminf(o.y, (float)(I[0].h - 1) - o.y));

@@ -78,31 +78,6 @@ __device__ __forceinline__ void stage_tile(uint8_t (*s)[IW], const uint8_t *src,
     }
 }
 
-// stage_tile without waiting: an interior tile is copied by 16-byte
-// cp.async chunks (global to shared, L1 bypassed) that complete at the
-// caller's cp.async wait; a border tile (reflect-101 mapping) or an
-// unaligned source is staged byte by byte with plain loads and stores.
-template <int IH, int IW>
-__device__ __forceinline__ void stage_tile_async(uint8_t (*s)[IW], const uint8_t *src, int w, int h, int pitch,
-                                                 int ix0, int iy0, bool vec_ok) {
-    const bool interior = vec_ok && ix0 >= 0 && ix0 + IW <= w && iy0 >= 0 && iy0 + IH <= h;
-    if (interior) {
-        constexpr int C16 = IW / 16;
-        const uint32_t sb = (uint32_t)__cvta_generic_to_shared(&s[0][0]);
-        for (int i = threadIdx.x; i < IH * C16; i += blockDim.x) {
-            const int r = i / C16, c = i - r * C16;
-            const uint8_t *g = src + (size_t)(iy0 + r) * pitch + ix0 + 16 * c;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sb + r * IW + 16 * c), "l"(g) : "memory");
-        }
-    } else {
-        for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
-            const int r = i / IW, c = i - r * IW;
-            const int sy = refl101(iy0 + r, h), sx = refl101(ix0 + c, w);
-            s[r][c] = __ldg(src + (size_t)sy * pitch + sx);
-        }
-    }
-}
-
 // Copy the staged rows [r0, r0 + nr) x staged columns [c0, c0 + 128) to
 // dst rows y0.. / columns x0.. (x0 a multiple of 128, dst rows 16-byte aligned).
 template <int IW>
@@ -344,16 +319,9 @@ struct PyrTileRef {
     int ix0, iy0;
 };
 
-// Resident CTAs per SM the batched pyramid kernel is register-budgeted for.
-constexpr int PD_MIN_BLOCKS = 5;
-
-// Tiles are software-pipelined: while a CTA computes tile t from one staging
-// buffer, the copies of its next tile (t + gridDim.x) into the other buffer
-// are in flight, so the global-load latency overlaps the vertical, Scharr and
-// horizontal passes instead of stalling the CTA at every tile.
 template <int GT>
-__global__ void __launch_bounds__(PD_THREADS, PD_MIN_BLOCKS) k_pyr_batch(const uint8_t *tab, int l) {
-    __shared__ __align__(16) uint8_t s_in[2][PD_IH][PD_IW];
+__global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l) {
+    __shared__ __align__(16) uint8_t s_in[PD_IH][PD_IW];
     __shared__ uint16_t s_v[PD_TH][PD_VW];
     __shared__ BLvlJob s_jobs[kJobsInSmem];
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
@@ -383,24 +351,9 @@ __global__ void __launch_bounds__(PD_THREADS, PD_MIN_BLOCKS) k_pyr_batch(const u
         r.ix0 = 2 * tx * PD_TW - 16;
         r.iy0 = 2 * ty * PD_TH - 2;
     };
-    auto issue = [&](int t, int buf) {
-        PyrTileRef r;
-        BFrame fr;
-        int tx, ty;
-        locate(t, r, fr, tx, ty);
-        stage_tile_async<PD_IH, PD_IW>(s_in[buf], r.src, r.w, r.h, r.pitch, r.ix0, r.iy0, r.vec_ok);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    issue(blockIdx.x, 0);
-    int buf = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, buf ^= 1) {
-        const int tn = t + gridDim.x;
-        if (tn < tiles)
-            issue(tn, buf ^ 1);
-        else
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // tile t's copies (this thread's) landed
-        __syncthreads();                                         // everyone's
+    pdl_wait();  // level l is the previous launch's output
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        if (t + (int)gridDim.x >= tiles) pdl_trigger();  // this CTA's last tile: the next launch may start
         PyrTileRef r;
         BFrame fr;
         int tx, ty;
@@ -409,9 +362,9 @@ __global__ void __launch_bounds__(PD_THREADS, PD_MIN_BLOCKS) k_pyr_batch(const u
         // level 0 also writes the pyramid's own level-0 copy, unless the
         // frame was built in place (the caller's image is that level)
         uint8_t *copy = (l == 0 && r.src != src.img) ? src.img : nullptr;
-        pyr_tile_compute<GT != VT_GRAD_NONE, GT>(src.w, src.h, dst.img, dst.pitch, src.grad, src.gpitch, copy,
-                                                 src.pitch, tx, ty, s_in[buf], s_v);
-        __syncthreads();  // s_in[buf] and s_v are free again
+        pyr_tile<GT != VT_GRAD_NONE, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad,
+                                         src.gpitch, copy, src.pitch, tx, ty, s_in, s_v);
+        __syncthreads();
     }
 }
 
@@ -508,7 +461,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_pyr_tail(const uint8_t *tab) {
     const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
     const BLvlJob *jobs =
         reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)(VT_MAX_LEVELS - 1) * H->cap_frames;
+    pdl_wait();  // level c is the previous launch's output
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+        if (j + (int)gridDim.x >= njobs) pdl_trigger();  // this CTA's last job
         const BLvlJob jb = jobs[j];
         const BFrame fr = frames[jb.frame];
         const int c = jb.aux;
@@ -594,23 +549,21 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
                                     TAIL_SMEM) == cudaSuccess;
     }();
     (void)attr;
-    for (int l = 0; l < tiled_launches; ++l) {
-        if (gtype == VT_GRAD_F16)
-            k_pyr_batch<VT_GRAD_F16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
-        else if (gtype == VT_GRAD_NONE)
-            k_pyr_batch<VT_GRAD_NONE><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
-        else
-            k_pyr_batch<VT_GRAD_S16><<<grid_pyr, PD_THREADS, 0, s>>>(dev_tab, l);
+    // every launch after the first overlaps its start with the previous one's
+    // end (programmatic dependent launch), except where an event is recorded
+    // in between for per-launch timing
+    auto pyr = gtype == VT_GRAD_F16 ? k_pyr_batch<VT_GRAD_F16>
+                                    : (gtype == VT_GRAD_NONE ? k_pyr_batch<VT_GRAD_NONE> : k_pyr_batch<VT_GRAD_S16>);
+    auto tail = gtype == VT_GRAD_F16 ? k_pyr_tail<VT_GRAD_F16>
+                                     : (gtype == VT_GRAD_NONE ? k_pyr_tail<VT_GRAD_NONE> : k_pyr_tail<VT_GRAD_S16>);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < tiled_launches && e == cudaSuccess; ++l) {
+        e = launch_pdl(pyr, grid_pyr, PD_THREADS, 0, s, l > 0 && !ev, dev_tab, l);
         if (ev && ev[l]) cudaEventRecord(ev[l], s);
     }
-    if (gtype == VT_GRAD_F16)
-        k_pyr_tail<VT_GRAD_F16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
-    else if (gtype == VT_GRAD_NONE)
-        k_pyr_tail<VT_GRAD_NONE><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
-    else
-        k_pyr_tail<VT_GRAD_S16><<<grid_tail, TAIL_THREADS, TAIL_SMEM, s>>>(dev_tab);
+    if (e == cudaSuccess) e = launch_pdl(tail, grid_tail, TAIL_THREADS, TAIL_SMEM, s, tiled_launches > 0 && !ev, dev_tab);
     if (ev && ev[tiled_launches]) cudaEventRecord(ev[tiled_launches], s);
-    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+    return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 
 int pyr_batch_blocks_per_sm() {
@@ -744,8 +697,11 @@ static vt_status build_impl(const uint8_t *img, int w, int h, int pitch, int lev
     vt_pyramid *p = *out;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const Level &L0 = p->lv[0];
-    cudaError_t e = cudaMemcpy2DAsync(L0.img, L0.pitch, img, pitch, w, h,
-                                      img_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (img == L0.img && pitch != L0.pitch) return VT_ERR_ARG;
+    // a frame already in level 0 (vt_pyramid_upload) is built in place
+    cudaError_t e = img == L0.img ? cudaSuccess
+                                  : cudaMemcpy2DAsync(L0.img, L0.pitch, img, pitch, w, h,
+                                                      img_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (fresh) {
@@ -801,6 +757,18 @@ vt_status vt_gradients(vt_pyramid *p, vt_grad_type t, void *cuda_stream) {
     vt_status st = launch_scharr(gj, blocks, (int)t, (cudaStream_t)cuda_stream);
     if (st == VT_OK) p->gtype = (int)t;
     return st;
+}
+
+vt_status vt_pyramid_upload(vt_pyramid *p, const uint8_t *img, int pitch, int img_on_device, void *cuda_stream) {
+    if (!p || !img || pitch < p->w) return VT_ERR_ARG;
+    const Level &L0 = p->lv[0];
+    if (cudaMemcpy2DAsync(L0.img, L0.pitch, img, pitch, p->w, p->h,
+                          img_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          (cudaStream_t)cuda_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    return VT_OK;
 }
 
 vt_status vt_pyramid_create(int w, int h, int levels, vt_pyramid **out) {

@@ -221,6 +221,16 @@ def vt_pyramid_build_grad(img, levels: int, grad_type: int = VT_GRAD_S16, stream
     return out if out is not None else Pyramid(hd.value)
 
 
+_sig("vt_pyramid_upload", i32, [vp, vp, i32, i32, vp])
+
+
+def vt_pyramid_upload(pyr: Pyramid, img, stream=None) -> None:
+    """Copy a frame (host or device array, the pyramid's w x h) into level 0
+    of ``pyr``; a build that then names level 0 as its image copies nothing."""
+    p, w, h, pitch, dev = _img_args(img)
+    _check(_lib.vt_pyramid_upload(pyr, p, pitch, dev, _stream(stream)), "vt_pyramid_upload")
+
+
 def vt_gradients(pyr: Pyramid, grad_type: int = VT_GRAD_S16, stream=None) -> None:
     _check(_lib.vt_gradients(pyr, grad_type, _stream(stream)), "vt_gradients")
 

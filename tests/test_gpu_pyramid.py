@@ -106,3 +106,42 @@ def test_rebuild_in_place_and_pitch():
         vt.vt_pyramid_build_grad(_img(301, 200, 3), 4, vt.VT_GRAD_S16, out=p)
     w, h, L, nbytes = p.info()
     assert (w, h, L) == (300, 200, 4) and nbytes > 0
+
+
+@pytest.mark.parametrize("w,h", [(752, 480), (1440, 1080), (97, 65)])
+def test_frame_uploaded_into_level0_builds_in_place(w, h):
+    """A frame copied into the pyramid's own level 0 (vt_pyramid_upload) and
+    built with level 0 named as its image gives the same pyramid and
+    gradients as a build from a separate image, through the single-pair call
+    and through the batched launches; level 0 keeps the frame.  Naming level
+    0 with another pitch is an argument error."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    img = _img(w, h, seed=7 * w + h)
+    L = _levels_for(w, h)
+    ref = oracle.build_pyramid(img, L)
+    a = vt.vt_pyramid_create(w, h, L)
+    vt.vt_pyramid_upload(a, img)
+    vt.vt_pyramid_build_grad(a.level(0), L, vt.VT_GRAD_S16, out=a)
+    b = vt.vt_pyramid_create(w, h, L)
+    vt.vt_pyramid_upload(b, torch.from_numpy(img).cuda())
+    batch = vt.Batch(2, 1)
+    vt.vt_batch_set(batch, [vt.frame_job(b.level(0), b)], [], vt.KltParams(levels=L))
+    vt.vt_batch_run(batch)
+    torch.cuda.synchronize()
+    for p in (a, b):
+        for l in range(L):
+            assert np.array_equal(p.level(l).cpu().numpy(), ref.levels[l]), l
+            g = p.grad(l).cpu().numpy()
+            assert np.array_equal(g[..., 0], ref.gx[l]) and np.array_equal(g[..., 1], ref.gy[l]), l
+    lv0 = a.level(0)
+    if lv0.stride(0) != w:  # a view of level 0 with another pitch
+        bad = torch.as_strided(lv0, (h, w - 1), (lv0.stride(0) - 1, 1)) if h > 1 else None
+        if bad is not None:
+            with pytest.raises(vt.VTError):
+                vt.vt_batch_set(batch, [vt.frame_job(bad, b)], [], vt.KltParams(levels=L))
+    batch.free()
+    a.free()
+    b.free()
