@@ -350,10 +350,17 @@ def run_native(a, rank, world, local_rank):
             tcur[0] += 1
             return e0.elapsed_time(e1)
 
-        best, timings = autotune(tr, tune_step, reps=5, warmup=2)
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        best, report = autotune(tr, tune_step, reps=5, warmup=2, sms=sms)
         t = tcur[0]
-        tune = {"warps_per_cta": best[0], "ctas_per_sm": best[1] or "occupancy limit",
-                "median_ms": {k: round(statistics.median(v), 4) for k, v in timings.items()}}
+        tune = {"warps_per_cta": best["shape"][0], "ctas_per_sm": best["shape"][1] or "occupancy limit",
+                "task_order": best["order"], "pyr_ctas_per_sm": best["pyr_ctas_per_sm"] or "occupancy limit",
+                "knob_medians_ms": report["knobs"], "default_ms": report["default_ms"],
+                "tuned_ms": report["tuned_ms"], "default_spread_ms": report["default_spread_ms"],
+                "tuned_spread_ms": report["tuned_spread_ms"],
+                "note": "step time (ms, median of 5) per knob value by coordinate descent from the default "
+                        "(4 warps/CTA at the occupancy limit, tasks in stream order, pyramid at the occupancy "
+                        "limit); default and pick then re-timed alternately"}
     for _ in range(a.warmup):
         batched_step(t)
         t += 1

@@ -627,11 +627,9 @@ struct Level64 {
 };
 
 // One level in FP64 (see kFp64Cond): the eigenvalue test and the Newton
-// iterations from the level's guess (gx, gy).  Kept out of line, with its
-// arguments and result passed by value, so that its FP64 registers do not
-// weigh on the FP32 path.
+// iterations from the level's guess (gx, gy).
 template <int WIN, int GT>
-__device__ __noinline__ Level64 track_level64(const Level Jl, const int max_iters, const float eps2,
+__device__ __forceinline__ Level64 track_level64(const Level Jl, const int max_iters, const float eps2,
                                               const float min_eig, float ux, float uy, float gx, float gy, int offi,
                                               int offg, int lane, KSmem<WIN> *smp) {
     constexpr int HW = WIN / 2;
@@ -686,11 +684,32 @@ __device__ __noinline__ Level64 track_level64(const Level Jl, const int max_iter
     return o;
 }
 
-// Track one point u = (ux0, uy0) from pyramid I to pyramid J.
-template <int WIN, int GT>
+template <int WIN, int GT, bool F64>
 __device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
                                             bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm, KOut &o,
-                                            bool want_err = true) {
+                                            bool want_err);
+
+// The point tracked again from the start by the FP64-capable tracker: out of
+// line, arguments and result by value, so that the FP32 tracker keeps no
+// FP64 state and nothing live across the call.
+template <int WIN, int GT>
+__device__ __noinline__ KOut track_point_f64(const Level *I, const Level *J, const KParams P, float ux0, float uy0,
+                                             bool has_guess, float gux, float guy, int lane, KSmem<WIN> *sm,
+                                             bool want_err) {
+    KOut o;
+    track_point<WIN, GT, true>(I, J, P, ux0, uy0, has_guess, gux, guy, lane, *sm, o, want_err);
+    return o;
+}
+
+// Track one point u = (ux0, uy0) from pyramid I to pyramid J.  The FP32
+// tracker (F64 = false) hands a point whose template at some level is
+// ill-conditioned (kFp64Cond) to track_point_f64, which tracks it again from
+// the start with that level in FP64; levels are deterministic, so the
+// coarser levels give the same results the second time.
+template <int WIN, int GT, bool F64>
+__device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
+                                            bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm, KOut &o,
+                                            bool want_err) {
     constexpr int HW = WIN / 2;
     constexpr float N = (float)(WIN * WIN);
     constexpr float unit = grad_unit<GT>();
@@ -749,6 +768,12 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         o.lmin = lmin * inv_norm;
         nux = nuy = 0.f;
         level64 = !(lmin * kFp64Cond >= lmax);  // ill-conditioned (or det <= 0): decide and track in FP64
+        if constexpr (!F64) {
+            if (level64) {
+                o = track_point_f64<WIN, GT>(I, J, P, ux0, uy0, has_guess, gux, guy, lane, &sm, want_err);
+                return;
+            }
+        }
         if (level64) {
             const Level64 r = track_level64<WIN, GT>(Jl, P.max_iters, P.eps2, P.min_eig, ux, uy, gx, gy, offi, offg,
                                                      lane, &sm);
@@ -861,7 +886,7 @@ __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, 
     for (int pass = 0; pass < npass; ++pass) {
         KOut r;
         // the backward pass only decides the status: its error is not an output
-        track_point<WIN, GT>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r, pass == 0);
+        track_point<WIN, GT, false>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r, pass == 0);
         if (pass == 0) {
             o = r;
             if (!r.status) return;

@@ -95,6 +95,11 @@ class BatchedTracker:
         self.batch_capacity = (max(1, nf), max(1, nf))
         self.batch = vt.Batch(*self.batch_capacity)
         self._flops = None
+        # order of the tasks in a run's work queue: "stream" (as the streams
+        # are listed) or "cost" (most pyramid levels first, then most
+        # points): the persistent tracking launch hands out points in task
+        # order, so costly points first leave cheaper ones for the tail
+        self.task_order = "stream"
 
     # ------------------------------------------------------------ descriptors
     def step_tables(self, sids, n_t, n_s, left=None, right=None, flops=None, kpt=None, kps=None, gate=True):
@@ -106,7 +111,7 @@ class BatchedTracker:
         (default: the stream's point buffers); flops: optional per-stream
         (t, s) int32 arrays; gate: False leaves the stereo gate out of this
         step even when the tracker has one."""
-        frames, tasks, gates = [], [], []
+        frames, tasks, gates, keyed = [], [], [], []
         for k, i in enumerate(sids):
             s = self.streams[i]
             cur = s.pyr[(s.built + 1) % 2]
@@ -119,17 +124,22 @@ class BatchedTracker:
             if n_t[k] > 0:
                 fl = flops[k][0] if flops is not None else None
                 pts = (kpt[k] if kpt is not None else s.kp_t)[:n_t[k]]
-                tasks.append(vt.track_task(prev, cur, pts, s.out_t[0], s.out_t[1], s.out_t[2], fb=True, flops=fl,
-                                           levels=s.levels, reason=s.out_t[3]))
+                keyed.append(((-s.levels, -n_t[k]), vt.track_task(prev, cur, pts, s.out_t[0], s.out_t[1], s.out_t[2],
+                                                                   fb=True, flops=fl, levels=s.levels,
+                                                                   reason=s.out_t[3])))
             if s.stereo and n_s[k] > 0:
                 fl = flops[k][1] if flops is not None else None
                 pts = (kps[k] if kps is not None else s.kp_s)[:n_s[k]]
-                tasks.append(vt.track_task(cur, s.pyr_r, pts, s.out_s[0], s.out_s[1], s.out_s[2], fb=True, flops=fl,
-                                           levels=s.levels, reason=s.out_s[3]))
+                keyed.append(((-s.levels, -n_s[k]), vt.track_task(cur, s.pyr_r, pts, s.out_s[0], s.out_s[1],
+                                                                   s.out_s[2], fb=True, flops=fl, levels=s.levels,
+                                                                   reason=s.out_s[3])))
                 if s.rig is not None and gate:
                     g = s.gate_out
                     gates.append(vt.gate_task(pts, s.out_s[0], s.rig, g[0], status_in=s.out_s[1], xyz=g[1],
                                               reason=g[2]))
+        if self.task_order == "cost":
+            keyed.sort(key=lambda kt: kt[0])  # stable: equal costs keep stream order
+        tasks = [t for _, t in keyed]
         fa = (vt.vt_frame_job * max(1, len(frames)))(*frames)
         ta = (vt.vt_track_task * max(1, len(tasks)))(*tasks)
         return fa, len(frames), ta, len(tasks), gates

@@ -1,5 +1,5 @@
-"""The launch-shape tuner on the GPU: every candidate launch shape gives
-bit-identical tracking results, and the tuner returns one of them."""
+"""The schedule tuner on the GPU: every candidate launch shape and task order
+gives bit-identical tracking results, and the tuner returns a schedule."""
 
 import numpy as np
 import pytest
@@ -51,6 +51,13 @@ def test_launch_shapes_do_not_change_results_and_tuner_picks_one():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    best, timings = autotune(tr, run_step, reps=2, warmup=1)
-    assert best in CANDIDATES and len(timings) == len(CANDIDATES)
+    # the cost-first task order gives the same results too
+    tr.task_order = "cost"
+    vt.vt_batch_config(tr.batch, 4, 0, 0)
+    one_step()
+    torch.cuda.synchronize()
+    assert [t.cpu().numpy().tobytes() for s in tr.streams for t in (s.out_t + s.out_s)] == ref
+    best, report = autotune(tr, run_step, reps=2, warmup=1, sms=torch.cuda.get_device_properties(0).multi_processor_count)
+    assert best["shape"] in CANDIDATES and best["order"] in ("stream", "cost")
+    assert set(report["knobs"]) == {"shape", "order", "pyr_ctas_per_sm"} and report["tuned_ms"] > 0
     tr.free()

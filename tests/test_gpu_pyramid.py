@@ -136,8 +136,8 @@ def test_frame_uploaded_into_level0_builds_in_place(w, h):
             assert np.array_equal(p.level(l).cpu().numpy(), ref.levels[l]), l
             g = p.grad(l).cpu().numpy()
             assert np.array_equal(g[..., 0], ref.gx[l]) and np.array_equal(g[..., 1], ref.gy[l]), l
-    lv0 = a.level(0)
-    if lv0.stride(0) != w:  # a view of level 0 with another pitch
+    lv0 = b.level(0)
+    if lv0.stride(0) != w:  # a view of b's level 0 with another pitch
         bad = torch.as_strided(lv0, (h, w - 1), (lv0.stride(0) - 1, 1)) if h > 1 else None
         if bad is not None:
             with pytest.raises(vt.VTError):
