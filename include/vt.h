@@ -517,6 +517,11 @@ VT_API vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr
  * skipped. */
 VT_API vt_status vt_batch_run_levels_timed(vt_batch *b, void *cuda_stream, void **events, int nevents);
 
+/* Wait for the last run of the staged tables and report whether any bounded
+ * wait of its kernels ran out (VT_ERR_TIMEOUT; the run's results are then
+ * incomplete), else VT_OK.  Synchronous. */
+VT_API vt_status vt_batch_check(vt_batch *b);
+
 /* Launch shape of the staged run and the number of kernel launches per run. */
 VT_API vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
                                int *launches_per_run);

@@ -15,6 +15,7 @@
 // batch: the host only rewrites the pinned tables between replays.  Two
 // staging buffers let the host prepare run t+1 while run t executes.
 #include <atomic>
+#include <cstddef>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -53,7 +54,52 @@ __global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARP
         KParams Pt = P;
         Pt.levels = t.levels;
         KOut o;
-        track_point_dir<WIN, GT>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, sm, o);
+        track_point_dir<WIN, GT, false>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, sm, o);
+        if (lane == 0) {
+            if (o.reason == kReasonPending) {  // left to k_klt_batch_f64
+                t.status[i] = kStatusPending;
+                continue;
+            }
+            t.pts_out[i] = make_float2(o.x, o.y);
+            t.status[i] = (uint8_t)o.status;
+            if (t.err) t.err[i] = o.status ? o.err : 0.f;
+            if (t.reason) t.reason[i] = (uint8_t)o.reason;
+            if (t.flops) t.flops[i] = klt_flops(WIN, o);
+        }
+    }
+}
+
+// The FP64-capable pass of a batched run (launched only when an accepted
+// template can be ill-conditioned, fp64_needed): warps stride over every
+// point of the run and track again, with ill-conditioned levels in FP64,
+// those the FP32 launch left pending.
+template <int WIN, int GT>
+__global__ void __launch_bounds__(128) k_klt_batch_f64(const uint8_t *tab) {
+    extern __shared__ __align__(16) uint8_t klt_smem[];
+    KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
+    const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
+    const BTask *tasks = reinterpret_cast<const BTask *>(tab + H->off_tasks);
+    const int *p0s = reinterpret_cast<const int *>(tab + H->off_prefix);
+    const int total = H->total_points, nt = H->ntasks;
+    const KParams P = H->P;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < total; p += nwarps) {
+        int lo = 0, hi = nt - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(p0s + mid) <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const BTask &t = tasks[lo];
+        const int i = p - t.p0;
+        if (t.n_dev && i >= __ldg(t.n_dev)) continue;
+        if (t.status[i] != kStatusPending) continue;
+        const float2 u = t.pts_in[i];
+        KParams Pt = P;
+        Pt.levels = t.levels;
+        KOut o;
+        track_point_dir<WIN, GT, true>(t.I, t.J, Pt, u.x, u.y, t.fb != 0, false, 0.f, 0.f, lane, sm, o);
         if (lane == 0) {
             t.pts_out[i] = make_float2(o.x, o.y);
             t.status[i] = (uint8_t)o.status;
@@ -62,6 +108,39 @@ __global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARP
             if (t.flops) t.flops[i] = klt_flops(WIN, o);
         }
     }
+}
+
+template <int WIN, int GT>
+static void launch_f64_win(const uint8_t *tab, int grid, cudaStream_t s) {
+    const size_t smem = 4 * sizeof(KSmem<WIN>);
+    static const bool attr = [smem] {  // once, thread-safe static initialisation
+        return cudaFuncSetAttribute(k_klt_batch_f64<WIN, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) == cudaSuccess;
+    }();
+    (void)attr;
+    k_klt_batch_f64<WIN, GT><<<grid, 128, smem, s>>>(tab);
+}
+
+template <int GT>
+static void launch_f64_gt(const uint8_t *tab, int win, int grid, cudaStream_t s) {
+    switch (win) {
+        case 9: launch_f64_win<9, GT>(tab, grid, s); break;
+        case 15: launch_f64_win<15, GT>(tab, grid, s); break;
+        case 21: launch_f64_win<21, GT>(tab, grid, s); break;
+        case 31: launch_f64_win<31, GT>(tab, grid, s); break;
+    }
+}
+
+// The FP64-capable pass over the run's pending points (stream-ordered after
+// the FP32 tracking launch).
+static vt_status launch_klt_f64(const uint8_t *tab, int win, int gtype, int grid, cudaStream_t s) {
+    if (gtype == VT_GRAD_F16)
+        launch_f64_gt<VT_GRAD_F16>(tab, win, grid, s);
+    else if (gtype == VT_GRAD_NONE)
+        launch_f64_gt<VT_GRAD_NONE>(tab, win, grid, s);
+    else
+        launch_f64_gt<VT_GRAD_S16>(tab, win, grid, s);
+    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 
 typedef void (*KltBatchFn)(const uint8_t *, int *);
@@ -102,10 +181,10 @@ static KltBatchKernel klt_batch_kernel(int win, int gtype, int warps) {
 }
 
 struct Topo {
-    int maxL, gtype, win, klt_warps, klt_grid, pyr_grid, gate;
+    int maxL, gtype, win, klt_warps, klt_grid, pyr_grid, gate, fp64;
     bool operator==(const Topo &o) const {
         return maxL == o.maxL && gtype == o.gtype && win == o.win && klt_warps == o.klt_warps &&
-               klt_grid == o.klt_grid && pyr_grid == o.pyr_grid && gate == o.gate;
+               klt_grid == o.klt_grid && pyr_grid == o.pyr_grid && gate == o.gate && fp64 == o.fp64;
     }
 };
 
@@ -188,8 +267,9 @@ static vt_status enqueue(vt_batch *b, int k, cudaStream_t s, cudaEvent_t *ev = n
     // launch), unless events are recorded for per-launch timing
     const cudaError_t e =
         launch_pdl(kb.fn, tp.klt_grid, tp.klt_warps * 32, kb.smem, s, !ev, (const uint8_t *)b->dev[k], b->counter + k);
-    if (ev && ev[3]) cudaEventRecord(ev[3], s);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VT_ERR_CUDA;
+    if (tp.fp64 && launch_klt_f64(b->dev[k], tp.win, tp.gtype, b->sms * 4, s) != VT_OK) return VT_ERR_CUDA;
+    if (ev && ev[3]) cudaEventRecord(ev[3], s);
     if (tp.gate) return launch_gate_batch(b->dev[k], b->gate_grid, s);
     return VT_OK;
 }
@@ -309,6 +389,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     H->P.eps2 = prm->eps * prm->eps;
     H->P.min_eig = prm->min_eig;
     H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
+    H->P.fp64 = fp64_needed(prm->min_eig);
     BFrame *bf = reinterpret_cast<BFrame *>(tab + H->off_frames);
     BLvlJob *jobs = reinterpret_cast<BLvlJob *>(tab + H->off_jobs);
     int maxL = 1, maxC = 0;
@@ -388,6 +469,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     tp.klt_grid = klt_grid(b, prm->win, (int)gtype);
     tp.pyr_grid = b->pyr_grid;
     tp.gate = 0;
+    tp.fp64 = H->P.fp64;
     b->staged = k;
     b->next = k ^ 1;
     b->fresh = true;
@@ -520,6 +602,18 @@ vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
     return VT_OK;
 }
 
+vt_status vt_batch_check(vt_batch *b) {
+    if (!b || b->staged < 0) return VT_ERR_ARG;
+    const int k = b->staged;
+    int fault = 0;
+    if ((b->ev_used[k] && cudaEventSynchronize(b->ev[k]) != cudaSuccess) ||
+        cudaMemcpy(&fault, b->dev[k] + offsetof(BatchHdr, fault), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    return fault ? VT_ERR_TIMEOUT : VT_OK;
+}
+
 vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
                         int *launches_per_run) {
     if (!b) return VT_ERR_ARG;
@@ -527,7 +621,8 @@ vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_pe
     if (klt_grid_ctas) *klt_grid_ctas = b->topo[k].klt_grid;
     if (klt_warps_per_cta) *klt_warps_per_cta = b->topo[k].klt_warps;
     if (pyr_grid_ctas) *pyr_grid_ctas = b->topo[k].pyr_grid;
-    if (launches_per_run) *launches_per_run = b->staged >= 0 ? b->topo[k].maxL + 1 + 1 + b->topo[k].gate : 0;
+    if (launches_per_run)
+        *launches_per_run = b->staged >= 0 ? b->topo[k].maxL + 1 + 1 + b->topo[k].fp64 + b->topo[k].gate : 0;
     return VT_OK;
 }
 
@@ -652,6 +747,7 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
     H->P.eps2 = prm->eps * prm->eps;
     H->P.min_eig = prm->min_eig;
     H->P.fb_thr2 = prm->fb_thr * prm->fb_thr;
+    H->P.fp64 = fp64_needed(prm->min_eig);
     int p0 = 0;
     for (int t = 0; t < ntasks; ++t) {
         const vt_track_task &tk = tasks[t];
@@ -681,5 +777,6 @@ extern "C" vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int 
     if (sms < 1) sms = 1;
     if (occ < 1) occ = 1;
     kb.fn<<<sms * occ, 4 * 32, kb.smem, s>>>(dev, reinterpret_cast<int *>(dev + kNoAllocCounterOff));
-    return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return VT_ERR_CUDA;
+    return T.hdr.P.fp64 ? launch_klt_f64(dev, prm->win, gtype, sms * 4, s) : VT_OK;
 }

@@ -118,7 +118,20 @@ struct KParams {
     float eps2;     // eps^2
     float min_eig;  // threshold on lambda_min / (win^2 255^2)
     float fb_thr2;  // fb_thr^2
+    int fp64;       // ill-conditioned levels go to the FP64-capable launch (see fp64_needed)
 };
+
+// Threshold on lambda_max / lambda_min of a level's gradient matrix above
+// which the level is decided and tracked in FP64.
+constexpr float kFp64Cond = 1e4f;
+
+// Whether an accepted template can be ill-conditioned at all.  Bilinear
+// samples of Scharr gradients are at most 4080/32 per component, so
+// lambda_max <= win^2 * 2 * 127.5^2, while an accepted template has
+// lambda_min >= min_eig * win^2 * 255^2: its condition number is at most
+// 0.5 / min_eig.  Below kFp64Cond (min_eig >= 5e-5, the default 1e-4
+// included) no level needs FP64 and the FP64-capable launch is skipped.
+inline bool fp64_needed(float min_eig) { return !(min_eig * kFp64Cond >= 0.5f); }
 
 // ------------------------------------------------------- batched job tables
 // Device-side tables of one batched run (vt_batch): a header followed by the
@@ -176,6 +189,7 @@ struct BatchHdr {
     int ngates, gate_points, off_gates, off_gprefix;
     vt_gate_params G;
     KParams P;
+    int fault;  // set on the device when a bounded wait of a launch of this run ran out
 };
 
 // Batched stereo gate (vt_stereo.cu): every gate task of the table at dev_tab,

@@ -23,19 +23,27 @@ struct KltArgs {
     KParams P;
 };
 
-template <int WIN, int GT, bool FB>
+// F64 = false: the FP32 tracker; a point with an ill-conditioned level is
+// left pending (status kStatusPending).  F64 = true: the second launch,
+// which tracks only the pending points, with such levels in FP64.
+template <int WIN, int GT, bool FB, bool F64>
 __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt(const __grid_constant__ KltArgs A) {
     extern __shared__ __align__(16) uint8_t klt_smem[];
     KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
     const int pt = blockIdx.x * KLT_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (pt >= A.n) return;
+    if (F64 && A.status[pt] != kStatusPending) return;
     const float2 p = A.pts_in[pt];
     KOut o;
     float2 g = make_float2(0.f, 0.f);
     const bool hg = !FB && A.guess != nullptr;
     if (hg) g = A.guess[pt];
-    track_point_dir<WIN, GT>(A.I.lv, A.J.lv, A.P, p.x, p.y, FB, hg, g.x, g.y, lane, sm, o);
+    track_point_dir<WIN, GT, F64>(A.I.lv, A.J.lv, A.P, p.x, p.y, FB, hg, g.x, g.y, lane, sm, o);
+    if (!F64 && o.reason == kReasonPending) {
+        if (lane == 0) A.status[pt] = kStatusPending;
+        return;
+    }
     if (lane == 0) {
         A.pts_out[pt] = make_float2(o.x, o.y);
         A.status[pt] = (uint8_t)o.status;
@@ -57,18 +65,26 @@ __global__ void k_fb_check(const float2 *p0, const float2 *p1, const uint8_t *sf
     out[i] = (uint8_t)(sf[i] && sb[i] && (dx * dx + dy * dy <= thr2));
 }
 
-template <int WIN, int GT, bool FB>
-static vt_status launch_one(const KltArgs &A, cudaStream_t s) {
+template <int WIN, int GT, bool FB, bool F64>
+static void launch_pass(const KltArgs &A, cudaStream_t s) {
     const int blocks = (A.n + KLT_WARPS - 1) / KLT_WARPS;
     const size_t smem = KLT_WARPS * sizeof(KSmem<WIN>);
     if (smem > 48 * 1024) {
         static const bool attr = [smem] {  // once, thread-safe static initialisation
-            return cudaFuncSetAttribute(k_klt<WIN, GT, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            return cudaFuncSetAttribute(k_klt<WIN, GT, FB, F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem) == cudaSuccess;
         }();
         (void)attr;
     }
-    k_klt<WIN, GT, FB><<<blocks, KLT_WARPS * 32, smem, s>>>(A);
+    k_klt<WIN, GT, FB, F64><<<blocks, KLT_WARPS * 32, smem, s>>>(A);
+}
+
+// The FP32 launch, then (only when an accepted template can be
+// ill-conditioned, fp64_needed) the FP64-capable launch over its pending points.
+template <int WIN, int GT, bool FB>
+static vt_status launch_one(const KltArgs &A, cudaStream_t s) {
+    launch_pass<WIN, GT, FB, false>(A, s);
+    if (A.P.fp64) launch_pass<WIN, GT, FB, true>(A, s);
     return cudaGetLastError() == cudaSuccess ? VT_OK : VT_ERR_CUDA;
 }
 
@@ -120,6 +136,7 @@ static vt_status track_common(const vt_pyramid *prev, const vt_pyramid *cur, con
     A.P.eps2 = prm->eps * prm->eps;
     A.P.min_eig = prm->min_eig;
     A.P.fb_thr2 = prm->fb_thr * prm->fb_thr;
+    A.P.fp64 = fp64_needed(prm->min_eig);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (prev->gtype == VT_GRAD_F16)
         return fb ? dispatch_win<VT_GRAD_F16, true>(A, s) : dispatch_win<VT_GRAD_F16, false>(A, s);

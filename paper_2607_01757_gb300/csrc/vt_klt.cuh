@@ -491,10 +491,9 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
 // level is tracked in FP64: the template and its gradients are sampled in
 // FP64 from the staged windows (kept in sm.t / sm.g) at every sweep, G, the
 // footprint moments, the 2x2 solve and the position update are FP64.  The
-// branch is warp-uniform; with the default eigenvalue threshold (1e-4) a
-// 21 x 21 window cannot exceed a condition number of about 5e3, so it is
-// taken only when a caller lowers the threshold.
-constexpr float kFp64Cond = 1e4f;
+// branch is warp-uniform; with the default eigenvalue threshold (1e-4) an
+// accepted template cannot exceed a condition number of 5e3 (fp64_needed),
+// so it is taken only when a caller lowers the threshold.
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -684,28 +683,18 @@ __device__ __forceinline__ Level64 track_level64(const Level Jl, const int max_i
     return o;
 }
 
-template <int WIN, int GT, bool F64>
-__device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
-                                            bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm, KOut &o,
-                                            bool want_err);
-
-// The point tracked again from the start by the FP64-capable tracker: out of
-// line, arguments and result by value, so that the FP32 tracker keeps no
-// FP64 state and nothing live across the call.
-template <int WIN, int GT>
-__device__ __noinline__ KOut track_point_f64(const Level *I, const Level *J, const KParams P, float ux0, float uy0,
-                                             bool has_guess, float gux, float guy, int lane, KSmem<WIN> *sm,
-                                             bool want_err) {
-    KOut o;
-    track_point<WIN, GT, true>(I, J, P, ux0, uy0, has_guess, gux, guy, lane, *sm, o, want_err);
-    return o;
-}
+// Internal reason of a point the FP32 tracker leaves to the FP64-capable one
+// (its status is written as kStatusPending until that second launch).
+constexpr int kReasonPending = 255;
+constexpr uint8_t kStatusPending = 2;
 
 // Track one point u = (ux0, uy0) from pyramid I to pyramid J.  The FP32
-// tracker (F64 = false) hands a point whose template at some level is
-// ill-conditioned (kFp64Cond) to track_point_f64, which tracks it again from
-// the start with that level in FP64; levels are deterministic, so the
-// coarser levels give the same results the second time.
+// tracker (F64 = false) stops at a level whose template is ill-conditioned
+// (kFp64Cond) and marks the point pending (kReasonPending); the kernels then
+// leave it to a second, FP64-capable launch (F64 = true) that tracks it again
+// from the start with such levels in FP64.  Levels are deterministic, so its
+// coarser levels give the same results the second time.  Keeping the FP64
+// code out of the FP32 kernels keeps their registers free of it.
 template <int WIN, int GT, bool F64>
 __device__ __forceinline__ void track_point(const Level *I, const Level *J, const KParams &P, float ux0, float uy0,
                                             bool has_guess, float gux, float guy, int lane, KSmem<WIN> &sm, KOut &o,
@@ -767,33 +756,34 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
         const float lmin = det / lmax;
         o.lmin = lmin * inv_norm;
         nux = nuy = 0.f;
-        level64 = !(lmin * kFp64Cond >= lmax);  // ill-conditioned (or det <= 0): decide and track in FP64
-        if constexpr (!F64) {
-            if (level64) {
-                o = track_point_f64<WIN, GT>(I, J, P, ux0, uy0, has_guess, gux, guy, lane, &sm, want_err);
-                return;
-            }
-        }
+        // ill-conditioned (or det <= 0): decided and tracked in FP64
+        level64 = P.fp64 && !(lmin * kFp64Cond >= lmax);
         if (level64) {
-            const Level64 r = track_level64<WIN, GT>(Jl, P.max_iters, P.eps2, P.min_eig, ux, uy, gx, gy, offi, offg,
-                                                     lane, &sm);
-            o.lmin = r.lmin;
-            o.iters += r.iters;
-            o.sweeps += r.sweeps;
-            nx64 = r.nx;
-            ny64 = r.ny;
-            if (r.reason != VT_TRACKED) {
+            if constexpr (!F64) {
                 o.status = 0;
-                o.reason = r.reason;
-                lost_level = l;
-                break;
+                o.reason = kReasonPending;
+                return;
+            } else {
+                const Level64 r = track_level64<WIN, GT>(Jl, P.max_iters, P.eps2, P.min_eig, ux, uy, gx, gy, offi,
+                                                         offg, lane, &sm);
+                o.lmin = r.lmin;
+                o.iters += r.iters;
+                o.sweeps += r.sweeps;
+                nx64 = r.nx;
+                ny64 = r.ny;
+                if (r.reason != VT_TRACKED) {
+                    o.status = 0;
+                    o.reason = r.reason;
+                    lost_level = l;
+                    break;
+                }
+                if (l > 0) {
+                    gx = (float)(2.0 * ((double)gx + nx64));
+                    gy = (float)(2.0 * ((double)gy + ny64));
+                    level64 = false;
+                }
+                continue;
             }
-            if (l > 0) {
-                gx = (float)(2.0 * ((double)gx + nx64));
-                gy = (float)(2.0 * ((double)gy + ny64));
-                level64 = false;
-            }
-            continue;
         }
         if (!(o.lmin >= P.min_eig) || !(det > 0.f)) {
             o.status = 0;
@@ -848,7 +838,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
     {
         const float sc = (float)(1 << lost_level);
         const float si = pow2neg(lost_level);
-        if (level64) {
+        if (F64 && level64) {
             o.x = (float)(((double)(ux0 * si) + (double)gx + nx64) * (double)sc);
             o.y = (float)(((double)(uy0 * si) + (double)gy + ny64) * (double)sc);
         } else {
@@ -875,7 +865,7 @@ __device__ __forceinline__ void track_point(const Level *I, const Level *J, cons
 // (pass 1) followed by the FB test.  One inlined copy of track_point serves
 // both passes, and every kernel (single-pair or batched) calls this function,
 // so a point's result does not depend on which kernel tracked it.
-template <int WIN, int GT>
+template <int WIN, int GT, bool F64>
 __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, const KParams &P, float ux0,
                                                 float uy0, bool fb, bool has_guess, float gux, float guy, int lane,
                                                 KSmem<WIN> &sm, KOut &o) {
@@ -886,7 +876,7 @@ __device__ __forceinline__ void track_point_dir(const Level *I, const Level *J, 
     for (int pass = 0; pass < npass; ++pass) {
         KOut r;
         // the backward pass only decides the status: its error is not an output
-        track_point<WIN, GT, false>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r, pass == 0);
+        track_point<WIN, GT, F64>(A, B, P, x, y, pass == 0 && has_guess, gux, guy, lane, sm, r, pass == 0);
         if (pass == 0) {
             o = r;
             if (!r.status) return;

@@ -14,6 +14,7 @@
 // tile serves the pyramid step and, in the fused variant, the gradients of
 // the source level.  Several levels / frames run in one launch through a
 // job table passed as a __grid_constant__ kernel parameter.
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -319,21 +320,67 @@ struct PyrTileRef {
     int ix0, iy0;
 };
 
+// Bulk-copy pipeline of the batched pyramid launches.  A CTA walks its tiles
+// (blockIdx.x, + gridDim.x, ...) through PD_STAGES staging buffers: while it
+// computes one tile, the rows of the next PD_STAGES - 1 tiles are in flight as
+// 1-D bulk copies (cp.async.bulk, issued by warp 0, completion counted in
+// bytes on the stage's mbarrier), so several tiles' loads overlap the
+// compute.  A tile that reaches a border (reflect-101) or comes from an
+// unaligned caller image is staged by all threads with plain loads instead;
+// its stage's barrier then completes its phase with a plain arrive, so every
+// use of a stage completes exactly one phase.
+constexpr int PD_STAGES = 3;
+constexpr long long kMbarSpinLimit = 1LL << 22;  // bounded waits (the copies take microseconds)
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of a barrier, giving up after kMbarSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kMbarSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 template <int GT>
-__global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l) {
-    __shared__ __align__(16) uint8_t s_in[PD_IH][PD_IW];
+__global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l, int *fault) {
+    __shared__ __align__(128) uint8_t s_in[PD_STAGES][PD_IH][PD_IW];
     __shared__ uint16_t s_v[PD_TH][PD_VW];
     __shared__ BLvlJob s_jobs[kJobsInSmem];
+    __shared__ __align__(8) uint64_t s_bar[PD_STAGES];
+    __shared__ int s_async[PD_STAGES];  // the stage's tile arrives by bulk copies
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const int njobs = H->njobs[l], tiles = H->ntiles[l];
     if ((int)blockIdx.x >= tiles) return;
     const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
     const BLvlJob *gjobs = reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)l * H->cap_frames;
     const bool in_smem = njobs <= kJobsInSmem;
-    if (in_smem) {
+    if (in_smem)
         for (int i = threadIdx.x; i < njobs; i += blockDim.x) s_jobs[i] = gjobs[i];
-        __syncthreads();
-    }
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&s_bar[0]);
+    if (threadIdx.x == 0)
+        for (int s = 0; s < PD_STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+    __syncthreads();
     const BLvlJob *jobs = in_smem ? s_jobs : gjobs;
     // where tile t's input lives, and its frame and tile coordinates
     auto locate = [&](int t, PyrTileRef &r, BFrame &fr, int &tx, int &ty) {
@@ -351,20 +398,72 @@ __global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, in
         r.ix0 = 2 * tx * PD_TW - 16;
         r.iy0 = 2 * ty * PD_TH - 2;
     };
-    pdl_wait();  // level l is the previous launch's output
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-        if (t + (int)gridDim.x >= tiles) pdl_trigger();  // this CTA's last tile: the next launch may start
+    auto interior = [](const PyrTileRef &r) {
+        return r.vec_ok && r.ix0 >= 0 && r.ix0 + PD_IW <= r.w && r.iy0 >= 0 && r.iy0 + PD_IH <= r.h;
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp 0: start the loads of the CTA's k-th tile into stage k % PD_STAGES
+    auto prefetch = [&](int k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= tiles) return;
+        const int st = k % PD_STAGES;
+        const uint32_t bar = bar0 + 8 * st;
         PyrTileRef r;
         BFrame fr;
         int tx, ty;
         locate(t, r, fr, tx, ty);
+        const bool async = interior(r);
+        if (lane == 0) {
+            s_async[st] = async;
+            if (async) {
+                // the stage was last read by generic loads: order them before the async-proxy writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_expect_tx(bar, PD_IH * PD_IW);
+            } else {
+                mbar_arrive(bar);  // staged by plain loads at its turn
+            }
+        }
+        __syncwarp();
+        if (async) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_in[st][0][0]);
+            for (int row = lane; row < PD_IH; row += 32)
+                bulk_copy_g2s(dst + row * PD_IW, r.src + (size_t)(r.iy0 + row) * r.pitch + r.ix0, PD_IW, bar);
+        }
+    };
+    pdl_wait();  // level l is the previous launch's output
+    if (warp == 0)
+        for (int k = 0; k < PD_STAGES - 1; ++k) prefetch(k);
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= tiles) break;
+        if (t + (int)gridDim.x >= tiles) pdl_trigger();  // this CTA's last tile: the next launch may start
+        const int st = k % PD_STAGES;
+        // the stage of tile k + PD_STAGES - 1 was freed by the previous iteration's closing barrier
+        if (warp == 0) prefetch(k + PD_STAGES - 1);
+        const bool landed = mbar_wait(bar0 + 8 * st, (uint32_t)(k / PD_STAGES) & 1u);
+        if (__syncthreads_or(!landed)) {
+            // a copy did not complete in time (the whole CTA agrees): report it,
+            // give the copies still in flight a bounded wait to land, and stop
+            if (threadIdx.x == 0) atomicOr(fault, 1);
+            for (int j = 1; j < PD_STAGES; ++j)
+                if (blockIdx.x + (k + j) * gridDim.x < tiles)
+                    mbar_wait(bar0 + 8 * ((k + j) % PD_STAGES), (uint32_t)((k + j) / PD_STAGES) & 1u);
+            return;
+        }
+        PyrTileRef r;
+        BFrame fr;
+        int tx, ty;
+        locate(t, r, fr, tx, ty);
+        if (!s_async[st]) stage_tile<PD_IH, PD_IW>(s_in[st], r.src, r.w, r.h, r.pitch, r.ix0, r.iy0, r.vec_ok);
+        __syncthreads();
         const Level src = fr.lv[l], dst = fr.lv[l + 1];
         // level 0 also writes the pyramid's own level-0 copy, unless the
         // frame was built in place (the caller's image is that level)
         uint8_t *copy = (l == 0 && r.src != src.img) ? src.img : nullptr;
-        pyr_tile<GT != VT_GRAD_NONE, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad,
-                                         src.gpitch, copy, src.pitch, tx, ty, s_in, s_v);
-        __syncthreads();
+        pyr_tile_compute<GT != VT_GRAD_NONE, GT>(src.w, src.h, dst.img, dst.pitch, src.grad, src.gpitch, copy,
+                                                 src.pitch, tx, ty, s_in[st], s_v);
+        __syncthreads();  // stage st and s_v are free again
     }
 }
 
@@ -552,13 +651,14 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
     // every launch after the first overlaps its start with the previous one's
     // end (programmatic dependent launch), except where an event is recorded
     // in between for per-launch timing
+    int *fault = const_cast<int *>(reinterpret_cast<const int *>(dev_tab + offsetof(BatchHdr, fault)));
     auto pyr = gtype == VT_GRAD_F16 ? k_pyr_batch<VT_GRAD_F16>
                                     : (gtype == VT_GRAD_NONE ? k_pyr_batch<VT_GRAD_NONE> : k_pyr_batch<VT_GRAD_S16>);
     auto tail = gtype == VT_GRAD_F16 ? k_pyr_tail<VT_GRAD_F16>
                                      : (gtype == VT_GRAD_NONE ? k_pyr_tail<VT_GRAD_NONE> : k_pyr_tail<VT_GRAD_S16>);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < tiled_launches && e == cudaSuccess; ++l) {
-        e = launch_pdl(pyr, grid_pyr, PD_THREADS, 0, s, l > 0 && !ev, dev_tab, l);
+        e = launch_pdl(pyr, grid_pyr, PD_THREADS, 0, s, l > 0 && !ev, dev_tab, l, fault);
         if (ev && ev[l]) cudaEventRecord(ev[l], s);
     }
     if (e == cudaSuccess) e = launch_pdl(tail, grid_tail, TAIL_THREADS, TAIL_SMEM, s, tiled_launches > 0 && !ev, dev_tab);

@@ -431,6 +431,14 @@ def vt_batch_run_levels_timed(b: Batch, stream, events) -> None:
     _check(_lib.vt_batch_run_levels_timed(b, _stream(stream), arr, len(events)), "vt_batch_run_levels_timed")
 
 
+_sig("vt_batch_check", i32, [vp])
+
+
+def vt_batch_check(b: Batch) -> None:
+    """Raise VTError(VT_ERR_TIMEOUT) if a bounded wait of the last run ran out."""
+    _check(_lib.vt_batch_check(b), "vt_batch_check")
+
+
 def vt_batch_info(b: Batch):
     g, w, pg, nl = i32(), i32(), i32(), i32()
     _check(_lib.vt_batch_info(b, C.byref(g), C.byref(w), C.byref(pg), C.byref(nl)), "vt_batch_info")
