@@ -517,11 +517,6 @@ VT_API vt_status vt_batch_run_timed(vt_batch *b, void *cuda_stream, void *ev_pyr
  * skipped. */
 VT_API vt_status vt_batch_run_levels_timed(vt_batch *b, void *cuda_stream, void **events, int nevents);
 
-/* Wait for the last run of the staged tables and report whether any bounded
- * wait of its kernels ran out (VT_ERR_TIMEOUT; the run's results are then
- * incomplete), else VT_OK.  Synchronous. */
-VT_API vt_status vt_batch_check(vt_batch *b);
-
 /* Launch shape of the staged run and the number of kernel launches per run. */
 VT_API vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,
                                int *launches_per_run);
@@ -566,6 +561,23 @@ VT_API vt_status vt_klt_track_tasks_noalloc(const vt_track_task *tasks, int ntas
  */
 VT_API vt_status vt_fp32_fma_probe(int iters, float *out, long long out_floats, long long *flops,
                                    void *cuda_stream);
+
+/*
+ * vt_copy_async - issue `n` memory copies on `cuda_stream`, in order, one
+ * cudaMemcpyAsync each (kind inferred from the addresses: device memory and
+ * pinned host memory); a request loop's per-request uploads and downloads
+ * in one call instead of one host-language call per copy.  Part of the
+ * serving runtime, not of the method.  Entries with bytes == 0 are skipped.
+ * VT_ERR_ARG for a null table or pointer, VT_ERR_CUDA if a copy fails to
+ * start (the copies before it stay queued).
+ */
+typedef struct vt_copy {
+    void *dst;
+    const void *src;
+    size_t bytes;
+} vt_copy;
+
+VT_API vt_status vt_copy_async(const vt_copy *copies, int n, void *cuda_stream);
 
 /* Human-readable name of a status code. */
 VT_API const char *vt_status_str(vt_status s);

@@ -602,16 +602,19 @@ vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
     return VT_OK;
 }
 
-vt_status vt_batch_check(vt_batch *b) {
-    if (!b || b->staged < 0) return VT_ERR_ARG;
-    const int k = b->staged;
-    int fault = 0;
-    if ((b->ev_used[k] && cudaEventSynchronize(b->ev[k]) != cudaSuccess) ||
-        cudaMemcpy(&fault, b->dev[k] + offsetof(BatchHdr, fault), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        return VT_ERR_CUDA;
+vt_status vt_copy_async(const vt_copy *copies, int n, void *cuda_stream) {
+    if (n < 0 || (n > 0 && !copies)) return VT_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (copies[i].bytes && (!copies[i].dst || !copies[i].src)) return VT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < n; ++i) {
+        if (!copies[i].bytes) continue;
+        if (cudaMemcpyAsync(copies[i].dst, copies[i].src, copies[i].bytes, cudaMemcpyDefault, s) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_CUDA;
+        }
     }
-    return fault ? VT_ERR_TIMEOUT : VT_OK;
+    return VT_OK;
 }
 
 vt_status vt_batch_info(const vt_batch *b, int *klt_grid_ctas, int *klt_warps_per_cta, int *pyr_grid_ctas,

@@ -189,7 +189,6 @@ struct BatchHdr {
     int ngates, gate_points, off_gates, off_gprefix;
     vt_gate_params G;
     KParams P;
-    int fault;  // set on the device when a bounded wait of a launch of this run ran out
 };
 
 // Batched stereo gate (vt_stereo.cu): every gate task of the table at dev_tab,

@@ -134,6 +134,9 @@ class Server:
                                       torch.empty(s.n_max, dtype=torch.uint8).pin_memory()))
                       for s in self.tr.streams]
         self.footprint = [self._footprint(i) for i in range(self.S)]
+        self._prm_c = self.params.c()
+        self._prm = vt.C.byref(self._prm_c)
+        self._addresses()
         self.slots = [dict(stream=torch.cuda.Stream(), event=torch.cuda.Event(), batch=vt.Batch(
             self.tr.batch_capacity[0], self.tr.batch_capacity[1]), reqs=None) for _ in range(slots)]
 
@@ -144,53 +147,77 @@ class Server:
         b += s.n_max * (8 + 8 + 1 + 4) * (2 if s.stereo else 1)  # points in/out, status, err
         return b
 
+    def _addresses(self):
+        """Device and pinned-host addresses of every stream's slots, frames,
+        keypoints and results (fixed for the server's lifetime)."""
+        self._dev = []
+        for i, s in enumerate(self.tr.streams):
+            d = dict(left=s.in_left.data_ptr(), bytes=s.w * s.h, kp_t=s.kp_t.data_ptr(),
+                     out_t=(s.out_t[0].data_ptr(), s.out_t[1].data_ptr()))
+            if s.stereo:
+                d.update(right=s.in_right.data_ptr(), kp_s=s.kp_s.data_ptr(),
+                         out_s=(s.out_s[0].data_ptr(), s.out_s[1].data_ptr()))
+            d["h_left"] = [x.data_ptr() for x in self.h_left[i]]
+            d["h_right"] = [x.data_ptr() if x is not None else 0 for x in self.h_right[i]]
+            d["h_kps"] = [k.data_ptr() for k in self.h_kps[i]]
+            d["n_kps"] = [int(k.shape[0]) for k in self.h_kps[i]]
+            d["h_out"] = [t.data_ptr() for t in self.h_out[i]]
+            self._dev.append(d)
+        self._tables = {}
+
+    def _request_copies(self, r):
+        """(uploads, downloads, n_t, n_s) of one request: its frame(s) and
+        keypoints into the stream's slots, its results back to the host."""
+        d = self._dev[r.sid]
+        up = [(d["left"], d["h_left"][r.frame], d["bytes"])]
+        down = []
+        nt = ns = 0
+        if r.prev_frame >= 0:
+            nt = d["n_kps"][r.prev_frame]
+            up.append((d["kp_t"], d["h_kps"][r.prev_frame], 8 * nt))
+            down += [(d["h_out"][0], d["out_t"][0], 8 * nt), (d["h_out"][1], d["out_t"][1], nt)]
+        if "right" in d:
+            ns = d["n_kps"][r.frame]
+            up += [(d["right"], d["h_right"][r.frame], d["bytes"]), (d["kp_s"], d["h_kps"][r.frame], 8 * ns)]
+            down += [(d["h_out"][2], d["out_s"][0], 8 * ns), (d["h_out"][3], d["out_s"][1], ns)]
+        return up, down, nt, ns
+
+    def _stream_tables(self, sid, nt, ns):
+        """The stream's frame and task descriptors for its next step (cached:
+        they depend only on the stream, which of its pyramids is current and
+        the point counts)."""
+        key = (sid, self.tr.streams[sid].built % 2, nt, ns)
+        t = self._tables.get(key)
+        if t is None:
+            fa, nf, ta, ntk, _ = self.tr.step_tables([sid], [nt], [ns])
+            t = ([fa[k] for k in range(nf)], [ta[k] for k in range(ntk)])
+            self._tables[key] = t
+        return t
+
     def _issue(self, slot, reqs):
-        torch = self.torch
         tr = self.tr
         cs = slot["stream"]
-        sids = [r.sid for r in reqs]
-        n_t, n_s = [], []
-        with torch.cuda.stream(cs):
-            for r in reqs:
-                s = tr.streams[r.sid]
-                s.in_left.copy_(self.h_left[r.sid][r.frame], non_blocking=True)
-                nt = 0
-                if r.prev_frame >= 0:
-                    kp = self.h_kps[r.sid][r.prev_frame]
-                    nt = kp.shape[0]
-                    s.kp_t[:nt].copy_(kp, non_blocking=True)
-                ns = 0
-                if s.stereo:
-                    s.in_right.copy_(self.h_right[r.sid][r.frame], non_blocking=True)
-                    kq = self.h_kps[r.sid][r.frame]
-                    ns = kq.shape[0]
-                    s.kp_s[:ns].copy_(kq, non_blocking=True)
-                n_t.append(nt)
-                n_s.append(ns)
-                r.n_features = nt
-                r.n_stereo = ns
-            fa, nf, ta, ntk, gates = tr.step_tables(sids, n_t, n_s)
-            code = vt._lib.vt_batch_set(slot["batch"], fa, nf, tr.grad_type, ta, ntk, vt.C.byref(self.params.c()))
-            if code != vt.VT_OK:
-                raise vt.VTError("vt_batch_set", code)
-            if gates:
-                vt.vt_batch_set_gates(slot["batch"], gates, tr.gate)
-            vt.vt_batch_run_graph(slot["batch"], cs)
-            tr.advance(sids)
-            for r, nt, ns in zip(reqs, n_t, n_s):
-                self._copy_out(r.sid, nt, ns)
-            slot["event"].record(cs)
+        up, down, frames, tasks = [], [], [], []
+        for r in reqs:
+            u, d, nt, ns = self._request_copies(r)
+            up += u
+            down += d
+            r.n_features = nt
+            r.n_stereo = ns
+            f, t = self._stream_tables(r.sid, nt, ns)
+            frames += f
+            tasks += t
+        vt.vt_copy_async(up, cs)
+        fa = (vt.vt_frame_job * max(1, len(frames)))(*frames)
+        ta = (vt.vt_track_task * max(1, len(tasks)))(*tasks)
+        code = vt._lib.vt_batch_set(slot["batch"], fa, len(frames), tr.grad_type, ta, len(tasks), self._prm)
+        if code != vt.VT_OK:
+            raise vt.VTError("vt_batch_set", code)
+        vt.vt_batch_run_graph(slot["batch"], cs)
+        tr.advance([r.sid for r in reqs])
+        vt.vt_copy_async(down, cs)
+        slot["event"].record(cs)
         slot["reqs"] = reqs
-
-    def _copy_out(self, sid, nt, ns):
-        """Queue the D2H copies of one request's results on the current stream."""
-        s, h = self.tr.streams[sid], self.h_out[sid]
-        if nt:
-            h[0][:nt].copy_(s.out_t[0][:nt], non_blocking=True)
-            h[1][:nt].copy_(s.out_t[1][:nt], non_blocking=True)
-        if ns:
-            h[2][:ns].copy_(s.out_s[0][:ns], non_blocking=True)
-            h[3][:ns].copy_(s.out_s[1][:ns], non_blocking=True)
 
     def serve(self, trace, realtime=True, max_batch=64, stall_s=60.0):
         """Run the trace; returns ServeStats.  With realtime=False every
@@ -298,23 +325,11 @@ class Server:
                     pass
             else:
                 r.t_arrive = 0.0
-            s = tr.streams[r.sid]
-            with torch.cuda.stream(cs):
-                s.in_left.copy_(self.h_left[r.sid][r.frame], non_blocking=True)
-                nt = 0
-                if r.prev_frame >= 0:
-                    kp = self.h_kps[r.sid][r.prev_frame]
-                    nt = kp.shape[0]
-                    s.kp_t[:nt].copy_(kp, non_blocking=True)
-                ns = 0
-                if s.stereo:
-                    s.in_right.copy_(self.h_right[r.sid][r.frame], non_blocking=True)
-                    kq = self.h_kps[r.sid][r.frame]
-                    ns = kq.shape[0]
-                    s.kp_s[:ns].copy_(kq, non_blocking=True)
-                tr.plain_step([r.sid], [nt], [ns], stream=cs)
-                tr.advance([r.sid])
-                self._copy_out(r.sid, nt, ns)
+            up, down, nt, ns = self._request_copies(r)
+            vt.vt_copy_async(up, cs)
+            tr.plain_step([r.sid], [nt], [ns], stream=cs)
+            tr.advance([r.sid])
+            vt.vt_copy_async(down, cs)
             cs.synchronize()
             td = now()
             stats.latencies_ms.append((td - r.t_arrive) * 1e3)

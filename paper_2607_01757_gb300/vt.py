@@ -431,12 +431,23 @@ def vt_batch_run_levels_timed(b: Batch, stream, events) -> None:
     _check(_lib.vt_batch_run_levels_timed(b, _stream(stream), arr, len(events)), "vt_batch_run_levels_timed")
 
 
-_sig("vt_batch_check", i32, [vp])
+class vt_copy(C.Structure):
+    _fields_ = [("dst", vp), ("src", vp), ("bytes", C.c_size_t)]
 
 
-def vt_batch_check(b: Batch) -> None:
-    """Raise VTError(VT_ERR_TIMEOUT) if a bounded wait of the last run ran out."""
-    _check(_lib.vt_batch_check(b), "vt_batch_check")
+_sig("vt_copy_async", i32, [C.POINTER(vt_copy), i32, vp])
+
+
+def vt_copy_async(copies, stream=None) -> None:
+    """Issue copies given as (dst_ptr, src_ptr, bytes) tuples or a ctypes
+    vt_copy array, in order, on ``stream``."""
+    if isinstance(copies, C.Array):
+        arr, n = copies, len(copies)
+    else:
+        lst = list(copies)
+        arr = (vt_copy * max(1, len(lst)))(*[vt_copy(d, s_, b) for d, s_, b in lst])
+        n = len(lst)
+    _check(_lib.vt_copy_async(arr, n, _stream(stream)), "vt_copy_async")
 
 
 def vt_batch_info(b: Batch):

@@ -80,3 +80,24 @@ def test_plain_serving_completes():
     st = srv.serve_plain(trace, realtime=False)
     assert st.served == 12 and st.features > 0
     srv.free()
+
+
+def test_copy_async_round_trip():
+    """vt_copy_async issues its copies in order on the stream: pinned host ->
+    device, device -> device, device -> pinned host; zero-byte entries are
+    skipped."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    rng = np.random.Generator(np.random.PCG64(5))
+    src = torch.from_numpy(rng.integers(0, 256, 100003, dtype=np.uint8)).pin_memory()
+    d1 = torch.zeros(100003, dtype=torch.uint8, device="cuda")
+    d2 = torch.zeros_like(d1)
+    back = torch.zeros(100003, dtype=torch.uint8).pin_memory()
+    vt.vt_copy_async([(d1.data_ptr(), src.data_ptr(), 100003), (0, 0, 0), (d2.data_ptr(), d1.data_ptr(), 100003),
+                      (back.data_ptr(), d2.data_ptr(), 100003)])
+    torch.cuda.synchronize()
+    assert torch.equal(back, src)
+    with pytest.raises(vt.VTError):
+        vt.vt_copy_async([(0, src.data_ptr(), 16)])
