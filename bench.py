@@ -121,6 +121,8 @@ def parse():
     ap.add_argument("--served-streams", type=int, default=64)
     ap.add_argument("--served-requests", type=int, default=10000)
     ap.add_argument("--served-budget-gb", type=float, default=20.0)
+    ap.add_argument("--served-slots", type=int, default=2,
+                    help="batches the served loop may have in flight (each on its own CUDA stream)")
     ap.add_argument("--served-rates", type=lambda v: [float(x) for x in v.split(",")], default=[1, 1.5, 2, 3, 4, 8, 16],
                     help="arrival-rate multipliers of the served sweep (comma-separated)")
     return ap.parse_args()
@@ -780,10 +782,10 @@ def run_served(a, wl, prm, barrier, max_over_ranks, sum_over_ranks):
     out = {"workload": f"{len(specs)} streams of the stream mix at 20-30 Hz (exponential jitter) times a rate "
                        f"multiplier, {a.served_requests} frame-pair requests per run, FB-checked temporal + stereo "
                        f"tracking, host frames in, host results out",
-           "budget_gb": a.served_budget_gb,
+           "budget_gb": a.served_budget_gb, "slots": a.served_slots,
            "features": "previous-frame keypoints tracked through the step (as the headline); stereo pairs apart"}
     budget = int(a.served_budget_gb * (1 << 30))
-    srv = Server(specs, frames, prm, budget_bytes=budget)
+    srv = Server(specs, frames, prm, budget_bytes=budget, slots=a.served_slots)
     warm = make_trace(specs, 2 * len(specs), seed=a.seed + 77, frames_per_stream=a.frames)
     srv.serve(warm, realtime=False)  # graph capture and first-touch outside the measurement
     # the plain arm's kernels (single-pair pyramid and tracking calls) loaded before its first measurement

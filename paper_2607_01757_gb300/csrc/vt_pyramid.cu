@@ -368,182 +368,6 @@ __global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, in
     }
 }
 
-// ---------------------------------------------------------------- strips
-// k_pyr_strip: the batched level launches without shared-memory staging or
-// barriers.  One warp builds one output tile (64 x 16 pixels of level l+1,
-// i.e. source columns x0 .. x0+127 and rows y0 .. y0+31 of level l): lane i
-// owns source columns x0 + 4i .. x0 + 4i + 3 and walks the 35 source rows
-// y0-2 .. y0+32 from top to bottom, reading each row once (one 32-bit word
-// per lane; the two columns left of the strip and the one right of it come
-// from lanes 0 and 31 and reach the neighbouring lanes by shuffles).  Per row
-// it
-//  * accumulates the vertical [1 4 6 4 1] sums of its columns as packed
-//    16-bit pairs (even and odd columns, at most 16 * 255 per lane) for the
-//    two output rows in flight, and emits an output row every second source
-//    row (horizontal [1 4 6 4 1] from its own and two shuffled neighbour
-//    columns, two output pixels per lane);
-//  * computes the Scharr responses of the previous row from a rolling window
-//    of three rows (dx = s(x+1) - s(x-1), s = 3 top + 10 mid + 3 bottom;
-//    dy = 3 d(x-1) + 10 d(x) + 3 d(x+1), d = bottom - top) and stores them
-//    as one 16-byte word per lane;
-//  * (level 0, unless built in place) stores the row as the pyramid's
-//    level-0 copy.
-// Rows outside the level are reflected (reflect-101); a strip that reaches
-// the level's left or right edge, or an unaligned caller image, reads its
-// bytes one by one through the reflected column index.  Integer arithmetic
-// throughout: bit-identical to the tile kernel and the oracle.
-constexpr int ST_WARPS = 8;
-constexpr unsigned kFullMask = 0xffffffffu;
-
-template <int GT>
-__device__ __forceinline__ void strip_tile(const uint8_t *src, int w, int h, int pitch, bool vec_ok, uint8_t *dst,
-                                           int dpitch, uint32_t *grad, int gpitch, uint8_t *copy, int cpitch, int tx,
-                                           int ty, int lane) {
-    constexpr bool GRAD = GT != VT_GRAD_NONE;
-    const int W = (w + 1) >> 1, H = (h + 1) >> 1;
-    const int x0 = 2 * PD_TW * tx, y0 = 2 * PD_TH * ty;
-    const int X0 = PD_TW * tx, Y0 = PD_TH * ty;
-    const int xl = x0 + 4 * lane;
-    const bool fast = vec_ok && x0 >= 4 && x0 + 2 * PD_TW + 4 <= w;
-    uint32_t acc_a[4] = {0u, 0u, 0u, 0u}, acc_b[4] = {0u, 0u, 0u, 0u};
-    int t6[6] = {0, 0, 0, 0, 0, 0}, m6[6] = {0, 0, 0, 0, 0, 0};  // rows r-2 and r-1: columns -1 .. 4
-#pragma unroll 1
-    for (int r = 0; r < 2 * PD_TH + 3; ++r) {
-        const int y = y0 - 2 + r;
-        const uint8_t *rp = src + (size_t)refl101(y, h) * pitch;
-        uint32_t w0, wl, wr;
-        if (fast) {
-            w0 = __ldg(reinterpret_cast<const uint32_t *>(rp + xl));
-            const uint32_t hl = lane == 0 ? __ldg(reinterpret_cast<const uint32_t *>(rp + x0 - 4)) : 0u;
-            const uint32_t hr = lane == 31 ? __ldg(reinterpret_cast<const uint32_t *>(rp + x0 + 2 * PD_TW)) : 0u;
-            wl = __shfl_up_sync(kFullMask, w0, 1);
-            wr = __shfl_down_sync(kFullMask, w0, 1);
-            if (lane == 0) wl = hl;
-            if (lane == 31) wr = hr;
-        } else {  // reflected columns (lanes beyond the level reflect too)
-            auto byte = [&](int k) { return (uint32_t)__ldg(rp + refl101(xl + k, w)); };
-            w0 = byte(0) | (byte(1) << 8) | (byte(2) << 16) | (byte(3) << 24);
-            wl = (byte(-2) << 16) | (byte(-1) << 24);
-            wr = byte(4);
-        }
-        // level-0 copy of the tile's own rows
-        if (copy != nullptr && r >= 2 && r < 2 * PD_TH + 2 && y < h && xl < w) {
-            uint8_t *d = copy + (size_t)y * cpitch + xl;
-            if (xl + 3 < w) {
-                *reinterpret_cast<uint32_t *>(d) = w0;
-            } else {
-                for (int q = 0; q < 4 && xl + q < w; ++q) d[q] = (uint8_t)(w0 >> (8 * q));
-            }
-        }
-        // vertical [1 4 6 4 1] on packed even / odd column pairs: own columns,
-        // and (lanes 0 and 31) the columns left / right of the strip
-        uint32_t x4[4];
-        x4[0] = w0 & 0x00FF00FFu;
-        x4[1] = (w0 >> 8) & 0x00FF00FFu;
-        x4[2] = (lane == 31 ? wr : wl) & 0x00FF00FFu;
-        x4[3] = (wl >> 8) & 0x00FF00FFu;
-        if ((r & 1) == 0) {
-            const int j = (r >> 1) - 2;  // output row completed by this source row
-            uint32_t v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = acc_a[k] + x4[k];
-                acc_a[k] = acc_b[k] + 6u * x4[k];
-                acc_b[k] = x4[k];
-            }
-            const uint32_t e_up = __shfl_up_sync(kFullMask, v[0], 1), o_up = __shfl_up_sync(kFullMask, v[1], 1);
-            const uint32_t e_dn = __shfl_down_sync(kFullMask, v[0], 1);
-            const int Y = Y0 + j;
-            if (j >= 0 && Y < H) {
-                const uint32_t vm2 = (lane == 0 ? v[2] : e_up) >> 16;
-                const uint32_t vm1 = (lane == 0 ? v[3] : o_up) >> 16;
-                const uint32_t vp4 = (lane == 31 ? v[2] : e_dn) & 0xffffu;
-                const uint32_t v0 = v[0] & 0xffffu, v1 = v[1] & 0xffffu, v2 = v[0] >> 16, v3 = v[1] >> 16;
-                const uint32_t o0 = (vm2 + v2 + 4u * (vm1 + v1) + 6u * v0 + 128u) >> 8;
-                const uint32_t o1 = (v0 + vp4 + 4u * (v1 + v3) + 6u * v2 + 128u) >> 8;
-                const int X = X0 + 2 * lane;
-                if (X < W) {
-                    uint8_t *d = dst + (size_t)Y * dpitch + X;
-                    if (X + 1 < W)
-                        *reinterpret_cast<uint16_t *>(d) = (uint16_t)(o0 | (o1 << 8));
-                    else
-                        *d = (uint8_t)o0;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                acc_a[k] += 4u * x4[k];
-                acc_b[k] += 4u * x4[k];
-            }
-        }
-        if constexpr (GRAD) {
-            // this row's columns -1 .. 4
-            int u6[6];
-            u6[0] = (int)(wl >> 24);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) u6[k + 1] = (int)((w0 >> (8 * k)) & 0xffu);
-            u6[5] = (int)(wr & 0xffu);
-            const int ym = y - 1;  // the Scharr row: the middle of rows r-2, r-1, r
-            if (r >= 3 && r < 2 * PD_TH + 3 && ym < h && xl < w) {
-                int sm[6], dd[6];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    sm[k] = 3 * (t6[k] + u6[k]) + 10 * m6[k];
-                    dd[k] = u6[k] - t6[k];
-                }
-                uint32_t gq[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    gq[q] = pack_grad<GT>(sm[q + 2] - sm[q], 3 * (dd[q] + dd[q + 2]) + 10 * dd[q + 1]);
-                uint32_t *d = grad + (size_t)ym * gpitch + xl;
-                if (xl + 3 < w) {
-                    *reinterpret_cast<uint4 *>(d) = make_uint4(gq[0], gq[1], gq[2], gq[3]);
-                } else {
-                    for (int q = 0; q < 4 && xl + q < w; ++q) d[q] = gq[q];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                t6[k] = m6[k];
-                m6[k] = u6[k];
-            }
-        }
-    }
-}
-
-template <int GT>
-__global__ void __launch_bounds__(ST_WARPS * 32, 4) k_pyr_strip(const uint8_t *tab, int l) {
-    __shared__ BLvlJob s_jobs[kJobsInSmem];
-    const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
-    const int njobs = H->njobs[l], tiles = H->ntiles[l];
-    const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
-    const BLvlJob *gjobs = reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)l * H->cap_frames;
-    const bool in_smem = njobs <= kJobsInSmem;
-    if (in_smem) {
-        for (int i = threadIdx.x; i < njobs; i += blockDim.x) s_jobs[i] = gjobs[i];
-        __syncthreads();
-    }
-    const BLvlJob *jobs = in_smem ? s_jobs : gjobs;
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * ST_WARPS;
-    pdl_wait();  // level l is the previous launch's output
-    for (int t = blockIdx.x * ST_WARPS + (threadIdx.x >> 5); t < tiles; t += nw) {
-        if (t + nw >= tiles) pdl_trigger();  // this warp's last tile
-        const BLvlJob jb = jobs[find_job(jobs, njobs, t)];
-        const BFrame fr = frames[jb.frame];
-        const Level src = fr.lv[l], dst = fr.lv[l + 1];
-        const int tt = t - jb.tile0;
-        const int ty = tt / jb.tiles_x, tx = tt - ty * jb.tiles_x;
-        const uint8_t *img = l == 0 ? fr.img : src.img;
-        // level 0 also writes the pyramid's own level-0 copy, unless the
-        // frame was built in place (the caller's image is that level)
-        uint8_t *copy = (l == 0 && img != src.img) ? src.img : nullptr;
-        strip_tile<GT>(img, src.w, src.h, l == 0 ? fr.pitch : src.pitch, l == 0 ? fr.vec_ok != 0 : true, dst.img,
-                       dst.pitch, src.grad, src.gpitch, copy, src.pitch, tx, ty, lane);
-    }
-}
-
 // ------------------------------------------------------------------ tail
 constexpr int TAIL_THREADS = 1024;
 constexpr int TAIL_A = kTailMaxPx;             // level c (<= kTailMaxPx pixels)
@@ -728,13 +552,13 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
     // every launch after the first overlaps its start with the previous one's
     // end (programmatic dependent launch), except where an event is recorded
     // in between for per-launch timing
-    auto pyr = gtype == VT_GRAD_F16 ? k_pyr_strip<VT_GRAD_F16>
-                                    : (gtype == VT_GRAD_NONE ? k_pyr_strip<VT_GRAD_NONE> : k_pyr_strip<VT_GRAD_S16>);
+    auto pyr = gtype == VT_GRAD_F16 ? k_pyr_batch<VT_GRAD_F16>
+                                    : (gtype == VT_GRAD_NONE ? k_pyr_batch<VT_GRAD_NONE> : k_pyr_batch<VT_GRAD_S16>);
     auto tail = gtype == VT_GRAD_F16 ? k_pyr_tail<VT_GRAD_F16>
                                      : (gtype == VT_GRAD_NONE ? k_pyr_tail<VT_GRAD_NONE> : k_pyr_tail<VT_GRAD_S16>);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < tiled_launches && e == cudaSuccess; ++l) {
-        e = launch_pdl(pyr, grid_pyr, ST_WARPS * 32, 0, s, l > 0 && !ev, dev_tab, l);
+        e = launch_pdl(pyr, grid_pyr, PD_THREADS, 0, s, l > 0 && !ev, dev_tab, l);
         if (ev && ev[l]) cudaEventRecord(ev[l], s);
     }
     if (e == cudaSuccess) e = launch_pdl(tail, grid_tail, TAIL_THREADS, TAIL_SMEM, s, tiled_launches > 0 && !ev, dev_tab);
@@ -744,7 +568,7 @@ vt_status launch_pyr_batch(const uint8_t *dev_tab, int tiled_launches, int gtype
 
 int pyr_batch_blocks_per_sm() {
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pyr_strip<VT_GRAD_S16>, ST_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pyr_batch<VT_GRAD_S16>, PD_THREADS, 0);
     return a;
 }
 
