@@ -42,8 +42,9 @@ SM_MAX_MHZ = 2070.0
 # for that workload and only while the sources still hash the same: a kernel
 # changed since the capture reports null.
 NCU_CAPTURES = {
-    "k_klt_batch": {"bytes": None, "date": None, "sources_sha1": None},
-    "pyramid": {"bytes": None, "date": None, "sources_sha1": None},
+    "k_klt_batch": {"bytes": 438682112 + 3838208, "date": "2026-12-04", "sources_sha1": "ca75a84b43fd2ab758480c8cf28a553466acbcb1"},
+    "pyramid": {"bytes": 62472448 + 264290304 + 15801344 + 7956992 + 3414784 + 0 + 1630464 + 256,
+                "date": "2026-12-04", "sources_sha1": "0999f480d2be8370202af864d6f447a8e8d58903"},
 }
 KERNEL_SOURCES = {
     "k_klt_batch": ["vt_klt.cuh", "vt_batch.cu", "vt_internal.cuh"],
