@@ -28,6 +28,8 @@ single-pair calls.
 
 from __future__ import annotations
 
+import functools
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -35,6 +37,25 @@ import numpy as np
 
 from . import vt
 from .engine import BatchedTracker
+
+
+def _without_gc(fn):
+    """Run a request loop with Python's cyclic garbage collector paused (one
+    collection before), so that no collection pause lands inside a
+    request's latency; reference counting still frees memory."""
+
+    @functools.wraps(fn)
+    def run(*args, **kwargs):
+        gc.collect()
+        was = gc.isenabled()
+        gc.disable()
+        try:
+            return fn(*args, **kwargs)
+        finally:
+            if was:
+                gc.enable()
+
+    return run
 
 
 @dataclass
@@ -219,6 +240,7 @@ class Server:
         slot["event"].record(cs)
         slot["reqs"] = reqs
 
+    @_without_gc
     def serve(self, trace, realtime=True, max_batch=64, stall_s=60.0):
         """Run the trace; returns ServeStats.  With realtime=False every
         request is available at time 0 (throughput mode)."""
@@ -311,6 +333,7 @@ class Server:
         stats.mean_batch = float(np.mean(batch_sizes)) if batch_sizes else 0.0
         return stats
 
+    @_without_gc
     def serve_plain(self, trace, realtime=True):
         """Baseline: every request alone, in arrival order, single-pair calls."""
         torch = self.torch
