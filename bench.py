@@ -114,6 +114,7 @@ def parse():
     ap.add_argument("--no-tracks", action="store_true")
     ap.add_argument("--no-frontend", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", choices=["gftt"], default=None,
                     help="run one section alone (profiler captures); prints that section only")
     ap.add_argument("--fe-cap", type=int, default=256, help="feature cap per stream of the front-end loop")
@@ -698,8 +699,11 @@ def run_native(a, rank, world, local_rank):
 
     # ---------------- CPU baseline (oracle), rank 0 at N = 1 only -------------
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(specs, frames, prm, a.cpu_seconds)
+        if not a.no_precision:
+            precision = precision_against_oracle(precision_gpu_runs(vt, torch))
 
     res = {
         "metric": METRIC,
@@ -759,6 +763,7 @@ def run_native(a, rank, world, local_rank):
         "track_bookkeeping": books,
         "frontend_loop": front,
         "cpu_baseline": cpu,
+        "precision": precision,
         "clocks": clocks,
     }
     tr.free()
@@ -915,6 +920,78 @@ def pyramid_launch_bytes(streams, grad, vt):
             per["tail"] = per.get("tail", 0) + b
     nt = max([k for k in per if k != "tail"], default=-1) + 1
     return [per.get(l, 0) for l in range(nt)] + [per.get("tail", 0)]
+
+
+def _precision_workloads():
+    """The precision configuration (1280x1024, 2000 keypoints, 5 levels): the
+    blurred pair with an exposure change, and its high-contrast variant
+    (step edges, exposure x1.3) where half-precision gradient storage rounds."""
+    import synth
+
+    blur = synth.make_config3_pair(seed=3)
+    cont = synth.make_config3_contrast_pair(seed=5)
+    return {"blur_exposure": (blur.left[0], blur.left[1], blur.kps[0]),
+            "high_contrast": (cont.I, cont.J, cont.pts)}
+
+
+def precision_gpu_runs(vt, torch):
+    """Forward-backward tracking of the precision workloads with int16 and
+    with FP16 gradient storage (single-pair calls)."""
+    import numpy as np
+
+    prm = vt.KltParams(win=21, levels=5, max_iters=30, eps=0.01, fb_thr=0.5)
+    out = {}
+    for name, (I, J, pts) in _precision_workloads().items():
+        res = {}
+        for label, gt in (("int16", vt.VT_GRAD_S16), ("fp16", vt.VT_GRAD_F16)):
+            pI, pJ = vt.vt_pyramid_build_grad(I, 5, gt), vt.vt_pyramid_build_grad(J, 5, gt)
+            p0 = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).cuda()
+            o = torch.zeros_like(p0)
+            st = torch.zeros(len(pts), dtype=torch.uint8, device="cuda")
+            vt.vt_klt_track_fb(pI, pJ, p0, prm, o, st)
+            torch.cuda.synchronize()
+            res[label] = (o.cpu().numpy(), st.cpu().numpy())
+            pI.free()
+            pJ.free()
+        out[name] = ((I, J, pts), res)
+    return out
+
+
+def precision_against_oracle(runs):
+    """The GPU's flow error against the FP64 oracle (on int16 gradients) per
+    precision workload and gradient storage: mean / p99 / max px over the
+    points both track, status agreement, and the fraction of the template
+    windows' gradient samples whose half-precision storage rounds (an odd
+    raw Scharr response above 2048 in magnitude)."""
+    import numpy as np
+
+    import oracle
+
+    out = {}
+    for name, ((I, J, pts), res) in runs.items():
+        pI, pJ = oracle.build_pyramid(I, 5), oracle.build_pyramid(J, 5)
+        t0 = time.perf_counter()
+        r = oracle.track_fb(pI, pJ, pts, 21, 5, 30, 0.01, 1e-4, 0.5)
+        dt = time.perf_counter() - t0
+        tot = rnd = 0
+        for lvl in range(5):
+            bad = ((np.abs(pI.gx[lvl].astype(np.int32)) > 2048) & (pI.gx[lvl] % 2 != 0)).astype(np.int32) + \
+                ((np.abs(pI.gy[lvl].astype(np.int32)) > 2048) & (pI.gy[lvl] % 2 != 0)).astype(np.int32)
+            h, w = bad.shape
+            for x, y in np.asarray(pts, np.float64) / 2 ** lvl:
+                ys = np.clip(np.arange(int(np.floor(y)) - 10, int(np.floor(y)) + 12), 0, h - 1)
+                xs = np.clip(np.arange(int(np.floor(x)) - 10, int(np.floor(x)) + 12), 0, w - 1)
+                rnd += int(bad[np.ix_(ys, xs)].sum())
+                tot += 2 * len(ys) * len(xs)
+        row = {"points": int(len(pts)), "oracle_s": dt, "fp16_rounded_window_samples": rnd / tot}
+        for label, (g_pts, g_st) in res.items():
+            both = (g_st == 1) & (r.status == 1)
+            d = np.hypot(*(g_pts[both] - r.fwd.pts[both]).T)
+            row[label] = {"mean_px": float(d.mean()), "p99_px": float(np.percentile(d, 99)), "max_px": float(d.max()),
+                          "status_equal": float((g_st == r.status).mean()), "tracked": int(both.sum())}
+        out[name] = row
+    return {"workload": "1280x1024, 2000 keypoints, 5 levels, window 21, forward-backward; oracle FP64 on int16 "
+                        "gradients", "rows": out}
 
 
 def cpu_model() -> str:

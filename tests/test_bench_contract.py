@@ -46,6 +46,11 @@ def test_native_small_run_line():
     for sec in ("gftt", "stereo_gate", "track_bookkeeping", "frontend_loop", "plain"):
         assert d[sec], sec
     assert d["config"]["launch_shape"]["warps_per_cta"] in (4, 8)
+    rows = d["precision"]["rows"]
+    assert set(rows) == {"blur_exposure", "high_contrast"}
+    for row in rows.values():
+        assert row["int16"]["max_px"] <= 0.05 and row["fp16"]["status_equal"] >= 0.99
+    assert rows["high_contrast"]["fp16_rounded_window_samples"] > 1e-3
 
 
 def test_cpu_baseline_uses_stream_levels_and_counts_iterations():
