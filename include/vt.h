@@ -499,7 +499,8 @@ VT_API vt_status vt_batch_run(vt_batch *b, void *cuda_stream);
 
 /* Same as vt_batch_run through a CUDA graph: captured (on an internal stream)
  * the first time a staging buffer is run with a given topology (deepest
- * pyramid, gradient type, window, launch shape), then replayed. */
+ * pyramid, gradient type, window, launch shape, stereo gate, FP64 pass), then
+ * replayed; each staging buffer keeps the graphs of up to 8 topologies. */
 VT_API vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream);
 
 /* vt_batch_run that also records the (nullable) CUDA events `ev_pyr0` /

@@ -180,6 +180,8 @@ static KltBatchKernel klt_batch_kernel(int win, int gtype, int warps) {
     return warps == 8 ? klt_batch_fn<VT_GRAD_S16, 8>(win) : klt_batch_fn<VT_GRAD_S16, 4>(win);
 }
 
+constexpr int kGraphsPerBuffer = 8;
+
 struct Topo {
     int maxL, gtype, win, klt_warps, klt_grid, pyr_grid, gate, fp64;
     bool operator==(const Topo &o) const {
@@ -204,8 +206,12 @@ struct vt_batch {
     int staged;  // buffer with the latest staged tables, -1 if none
     bool fresh;  // the staged tables have not been enqueued yet (gates may still be set)
     Topo topo[2];
-    cudaGraphExec_t exec[2];
-    Topo exec_topo[2];
+    // instantiated graphs per staging buffer, one per topology seen (runs of
+    // different stream mixes alternate topologies, e.g. a request loop's
+    // batches), replaced round robin when full
+    cudaGraphExec_t exec[2][kGraphsPerBuffer];
+    Topo exec_topo[2][kGraphsPerBuffer];
+    int exec_next[2];
     cudaStream_t cap;
     int sms;
     int klt_warps;        // warps per CTA of the KLT launch (4 or 8)
@@ -316,7 +322,8 @@ void vt_batch_free(vt_batch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     for (int k = 0; k < 2; ++k) {
-        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        for (int j = 0; j < kGraphsPerBuffer; ++j)
+            if (b->exec[k][j]) cudaGraphExecDestroy(b->exec[k][j]);
         if (b->host[k]) cudaFreeHost(b->host[k]);
         if (b->dev[k]) cudaFree(b->dev[k]);
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
@@ -568,10 +575,15 @@ vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
     const int k = b->staged;
     b->fresh = false;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (!b->exec[k] || !(b->exec_topo[k] == b->topo[k])) {
-        if (b->exec[k]) {
-            cudaGraphExecDestroy(b->exec[k]);
-            b->exec[k] = nullptr;
+    int slot = -1;
+    for (int j = 0; j < kGraphsPerBuffer && slot < 0; ++j)
+        if (b->exec[k][j] && b->exec_topo[k][j] == b->topo[k]) slot = j;
+    if (slot < 0) {
+        slot = b->exec_next[k];
+        b->exec_next[k] = (slot + 1) % kGraphsPerBuffer;
+        if (b->exec[k][slot]) {
+            cudaGraphExecDestroy(b->exec[k][slot]);
+            b->exec[k][slot] = nullptr;
         }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -585,16 +597,16 @@ vt_status vt_batch_run_graph(vt_batch *b, void *cuda_stream) {
             if (g) cudaGraphDestroy(g);
             return st != VT_OK ? st : VT_ERR_CUDA;
         }
-        e = cudaGraphInstantiate(&b->exec[k], g, 0);
+        e = cudaGraphInstantiate(&b->exec[k][slot], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            b->exec[k] = nullptr;
+            b->exec[k][slot] = nullptr;
             return VT_ERR_CUDA;
         }
-        b->exec_topo[k] = b->topo[k];
+        b->exec_topo[k][slot] = b->topo[k];
     }
-    if (cudaGraphLaunch(b->exec[k], s) != cudaSuccess || cudaEventRecord(b->ev[k], s) != cudaSuccess) {
+    if (cudaGraphLaunch(b->exec[k][slot], s) != cudaSuccess || cudaEventRecord(b->ev[k], s) != cudaSuccess) {
         cudaGetLastError();
         return VT_ERR_CUDA;
     }
