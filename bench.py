@@ -125,7 +125,7 @@ def parse():
     ap.add_argument("--served-budget-gb", type=float, default=20.0)
     ap.add_argument("--served-slots", type=int, default=2,
                     help="batches the served loop may have in flight (each on its own CUDA stream)")
-    ap.add_argument("--served-rates", type=lambda v: [float(x) for x in v.split(",")], default=[1, 1.5, 2, 3, 4, 8, 16],
+    ap.add_argument("--served-rates", type=lambda v: [float(x) for x in v.split(",")], default=[1, 1.5, 2, 2.5, 3, 4, 8, 16],
                     help="arrival-rate multipliers of the served sweep (comma-separated)")
     return ap.parse_args()
 
@@ -702,8 +702,8 @@ def run_native(a, rank, world, local_rank):
     precision = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(specs, frames, prm, a.cpu_seconds)
-        if not a.no_precision:
-            precision = precision_against_oracle(precision_gpu_runs(vt, torch))
+    if rank == 0 and world == 1 and not a.no_precision:
+        precision = precision_against_oracle(precision_gpu_runs(vt, torch))
 
     res = {
         "metric": METRIC,
@@ -792,8 +792,13 @@ def run_served(a, wl, prm, barrier, max_over_ranks, sum_over_ranks):
            "features": "previous-frame keypoints tracked through the step (as the headline); stereo pairs apart"}
     budget = int(a.served_budget_gb * (1 << 30))
     srv = Server(specs, frames, prm, budget_bytes=budget, slots=a.served_slots)
+    # graph capture (one graph per batch topology and staging buffer) and
+    # first touch outside the measurement: all-at-once batches, then
+    # one-request batches as a real-time trace mostly issues
     warm = make_trace(specs, 2 * len(specs), seed=a.seed + 77, frames_per_stream=a.frames)
-    srv.serve(warm, realtime=False)  # graph capture and first-touch outside the measurement
+    srv.serve(warm, realtime=False)
+    srv.serve(make_trace(specs, 4 * len(specs), seed=a.seed + 79, frames_per_stream=a.frames), realtime=False,
+              max_batch=1)
     # the plain arm's kernels (single-pair pyramid and tracking calls) loaded before its first measurement
     srv.serve_plain(make_trace(specs, 2 * len(specs), seed=a.seed + 78, frames_per_stream=a.frames), realtime=False)
     keys = ("features_per_s", "stereo_pairs_per_s", "p50_ms", "p99_ms", "p999_ms", "mean_batch_requests",
@@ -1134,6 +1139,7 @@ def main():
     if a.small:
         a.streams = min(a.streams, 4)
         a.no_cpu = True
+        a.no_precision = True
     if a.only == "gftt":  # the detector section alone (for profiler captures)
         import torch
 

@@ -46,11 +46,24 @@ def test_native_small_run_line():
     for sec in ("gftt", "stereo_gate", "track_bookkeeping", "frontend_loop", "plain"):
         assert d[sec], sec
     assert d["config"]["launch_shape"]["warps_per_cta"] in (4, 8)
-    rows = d["precision"]["rows"]
+
+
+@pytest.mark.gpu
+def test_precision_row():
+    """The bench's precision row: int16 and FP16 gradient storage against the
+    FP64 oracle on both precision workloads."""
+    import torch
+
+    import bench
+    import paper_2607_01757_gb300 as vt
+
+    d = bench.precision_against_oracle(bench.precision_gpu_runs(vt, torch))
+    rows = d["rows"]
     assert set(rows) == {"blur_exposure", "high_contrast"}
     for row in rows.values():
         assert row["int16"]["max_px"] <= 0.05 and row["fp16"]["status_equal"] >= 0.99
     assert rows["high_contrast"]["fp16_rounded_window_samples"] > 1e-3
+    assert rows["blur_exposure"]["fp16_rounded_window_samples"] == 0.0
 
 
 def test_cpu_baseline_uses_stream_levels_and_counts_iterations():

@@ -253,3 +253,43 @@ def test_batched_pyramids_at_workload_sizes(grad):
                 ex = (ref.gx[l] / 32.0).astype(np.float16)
                 assert np.array_equal(g[..., 0].view(np.uint16), ex.view(np.uint16)), (img.shape, l)
     b.free()
+
+
+def test_levels_timed_run_and_fma_probe():
+    """vt_batch_run_levels_timed records an event after every pyramid launch
+    of the staged run (and refuses too few events); the FP32 FMA probe
+    returns its FLOP count and runs at a plausible rate."""
+    import torch
+
+    vt = _vt()
+    streams = _streams(3, 51, torch, vt)
+    prm = _prm(vt, min(s.spec.levels for s in streams))
+    b = vt.Batch(32, 32)
+    frames, tasks = _stage(vt, streams, prm)
+    vt.vt_batch_set(b, frames, tasks, prm)
+    n_pyr = vt.vt_batch_info(b)["launches_per_run"] - 1
+    ev = []
+    for _ in range(4 + n_pyr):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        ev.append(e)
+    with pytest.raises(vt.VTError):
+        vt.vt_batch_run_levels_timed(b, None, ev[:3 + n_pyr])
+    vt.vt_batch_run_levels_timed(b, None, ev)
+    torch.cuda.synchronize()
+    ms = [ev[0].elapsed_time(ev[4])] + [ev[4 + j - 1].elapsed_time(ev[4 + j]) for j in range(1, n_pyr)]
+    assert all(m >= 0 for m in ms) and ev[0].elapsed_time(ev[1]) >= sum(ms) * 0.999
+    b.free()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = torch.empty(sms * 2048, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fl = vt.vt_fp32_fma_probe(512, out)
+    e1.record()
+    torch.cuda.synchronize()
+    assert fl == sms * 8 * 256 * 8 * 8 * 512 * 2
+    tflops = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+    assert 5.0 < tflops < 200.0, tflops
+    assert torch.isfinite(out).all()
+    with pytest.raises(vt.VTError):
+        vt.vt_fp32_fma_probe(512, out[:100])
