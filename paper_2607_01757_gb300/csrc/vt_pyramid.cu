@@ -96,6 +96,62 @@ __device__ __forceinline__ void copy_out(const uint8_t (*s)[IW], int r0, int c0,
     }
 }
 
+// Scharr (int16 output) of 4 consecutive columns x .. x+3 and 4 rows y0 ..
+// y0+3 of the staged tile, two pixels per 32-bit operation.  A word holds two
+// columns two apart in its 16-bit lanes: (x, x+2), (x+1, x+3), and the edge
+// columns (x-1, x+4).  Per lane, the vertical smoothing V = 3 top + 10 mid +
+// 3 bottom is at most 4080 and the biased difference D = bottom - top + 2048
+// lies in [1793, 2303], so
+//   dx + 32768 = V(x+1) - V(x-1) + 32768,
+//   dy + 32768 = 3 D(x-1) + 10 D(x) + 3 D(x+1)      (bias 16 * 2048)
+// both lie in [28688, 36848]: no lane ever borrows from or carries into its
+// neighbour, and flipping bit 15 of a lane turns the biased value into the
+// int16 two's complement of dx or dy.  Same results as the scalar form.
+// `sr0` is the staged row above y0; `xr` the staged column offset of x.
+__device__ __forceinline__ void scharr_4x4_s16(const uint8_t (*s)[PD_IW], int sr0, int xr, int x, int y0, int w,
+                                               int h, uint32_t *grad, int gpitch) {
+    uint32_t c13[3], c24[3], ce[3];  // rows above, centre, below
+    auto load_row = [&](int sr, uint32_t &a13, uint32_t &a24, uint32_t &ae) {
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(&s[sr][12 + xr]);
+        const uint32_t a = wp[0], b = wp[1], c = wp[2];  // columns x-4 .. x+7
+        a13 = b & 0x00FF00FFu;
+        a24 = (b >> 8) & 0x00FF00FFu;
+        ae = (a >> 24) | ((c << 16) & 0x00FF0000u);
+    };
+    load_row(sr0, c13[0], c24[0], ce[0]);
+    load_row(sr0 + 1, c13[1], c24[1], ce[1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        load_row(sr0 + 2 + i, c13[2], c24[2], ce[2]);
+        const int y = y0 + i;
+        if (y < h && x < w) {
+            const uint32_t v13 = 3u * (c13[0] + c13[2]) + 10u * c13[1];
+            const uint32_t v24 = 3u * (c24[0] + c24[2]) + 10u * c24[1];
+            const uint32_t ve = 3u * (ce[0] + ce[2]) + 10u * ce[1];
+            const uint32_t d13 = c13[2] + 0x08000800u - c13[0];
+            const uint32_t d24 = c24[2] + 0x08000800u - c24[0];
+            const uint32_t de = ce[2] + 0x08000800u - ce[0];
+            const uint32_t vm = __byte_perm(ve, v24, 0x5410), vp = __byte_perm(v13, ve, 0x7632);  // (x-1, x+1), (x+2, x+4)
+            const uint32_t dm = __byte_perm(de, d24, 0x5410), dp = __byte_perm(d13, de, 0x7632);
+            const uint32_t dx13 = (v24 + 0x80008000u - vm) ^ 0x80008000u;  // columns (x, x+2)
+            const uint32_t dx24 = (vp + 0x80008000u - v13) ^ 0x80008000u;  // columns (x+1, x+3)
+            const uint32_t dy13 = (3u * (dm + d24) + 10u * d13) ^ 0x80008000u;
+            const uint32_t dy24 = (3u * (d13 + dp) + 10u * d24) ^ 0x80008000u;
+            const uint32_t g0 = __byte_perm(dx13, dy13, 0x5410), g2 = __byte_perm(dx13, dy13, 0x7632);
+            const uint32_t g1 = __byte_perm(dx24, dy24, 0x5410), g3 = __byte_perm(dx24, dy24, 0x7632);
+            uint32_t *d = grad + (size_t)y * gpitch + x;
+            if (x + 3 < w) {
+                *reinterpret_cast<uint4 *>(d) = make_uint4(g0, g1, g2, g3);
+            } else {
+                const uint32_t gq[4] = {g0, g1, g2, g3};
+                for (int q = 0; q < 4 && x + q < w; ++q) d[q] = gq[q];
+            }
+        }
+        c13[0] = c13[1], c24[0] = c24[1], ce[0] = ce[1];
+        c13[1] = c13[2], c24[1] = c24[2], ce[1] = ce[2];
+    }
+}
+
 // One output tile (tx, ty) of the pyramid step src -> dst; with GRAD also the
 // Scharr planes of src over the matching 2*TW x 2*TH region, and with `copy`
 // a copy of that src region (level 0 of a pyramid built from a caller image).
@@ -106,11 +162,13 @@ __device__ __forceinline__ void copy_out(const uint8_t (*s)[IW], int r0, int c0,
 //  * vertical [1 4 6 4 1] pass on 32-bit words: the even and odd bytes of a
 //    word are summed as two packed 16-bit lanes (at most 16 * 255 = 4080, no
 //    carry between lanes), 4 columns per operation;
-//  * horizontal pass: 4 outputs per thread from 6 packed column pairs;
+//  * horizontal pass: 4 outputs per thread from 6 packed column pairs, two
+//    outputs per 32-bit operation;
 //  * Scharr: each thread owns 4 columns x 4 rows and slides a 3-row window of
 //    6 bytes per row (3 aligned word loads per row), with the separable form
 //    dx = s(x+1) - s(x-1), s = 3 top + 10 mid + 3 bottom, and
-//    dy = 3 d(x-1) + 10 d(x) + 3 d(x+1), d = bottom - top.
+//    dy = 3 d(x-1) + 10 d(x) + 3 d(x+1), d = bottom - top; int16 planes two
+//    pixels per 32-bit operation (scharr_4x4_s16), half planes per pixel.
 template <bool GRAD, int GT>
 __device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int dpitch, uint32_t *grad, int gpitch,
                                                  uint8_t *copy, int cpitch, int tx, int ty,
@@ -148,7 +206,10 @@ __device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int
         uint32_t *out = reinterpret_cast<uint32_t *>(&s_v[r][0]) + 2 * j;
         *reinterpret_cast<uint2 *>(out) = make_uint2(__byte_perm(sl, sh, 0x5410), __byte_perm(sl, sh, 0x7632));
     }
-    if constexpr (GRAD) {
+    if constexpr (GRAD && GT == VT_GRAD_S16) {
+        const int g = threadIdx.x & 31, rg = threadIdx.x >> 5;
+        scharr_4x4_s16(s_in, 4 * rg + 1, 4 * g, 2 * ox0 + 4 * g, 2 * oy0 + 4 * rg, w, h, grad, gpitch);
+    } else if constexpr (GRAD) {
         const int g = threadIdx.x & 31, rg = threadIdx.x >> 5;
         const int xr = 4 * g, x = 2 * ox0 + xr;
         int t0[6], t1[6], t2[6];
@@ -201,25 +262,30 @@ __device__ __forceinline__ void pyr_tile_compute(int w, int h, uint8_t *dst, int
         const int r = threadIdx.x >> 4, x4 = (threadIdx.x & 15) * 4;
         const int oy = oy0 + r, ox = ox0 + x4;
         if (oy < H && ox < W) {
+            // two outputs per 32-bit operation: lanes (o0, o1) and (o2, o3);
+            // word k of the row holds s_v columns (2k, 2k+1) after the
+            // offset, and output q needs columns 2q .. 2q+4, so lane pairs
+            // (c, c+2) are gathered by byte permutes; a lane's sum is at
+            // most 16 * 4080 = 65280 and never carries into its neighbour
             const uint32_t *pr = reinterpret_cast<const uint32_t *>(&s_v[r][0]) + x4 + 1;
-            uint32_t v[12];
+            uint32_t p[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const uint32_t pk = pr[k];
-                v[2 * k] = pk & 0xffffu;
-                v[2 * k + 1] = pk >> 16;
-            }
-            uint32_t o[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t sum = v[2 * q] + v[2 * q + 4] + 4u * (v[2 * q + 1] + v[2 * q + 3]) + 6u * v[2 * q + 2];
-                o[q] = (sum + 128u) >> 8;
-            }
+            for (int k = 0; k < 6; ++k) p[k] = pr[k];
+            auto lo2 = [](uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5410); };
+            auto hi2 = [](uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); };
+            auto down2 = [](uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4) {
+                const uint32_t sum = w0 + w4 + 0x00800080u + 4u * (w1 + w3) + 6u * w2;
+                return (sum >> 8) & 0x00FF00FFu;
+            };
+            const uint32_t w4 = lo2(p[2], p[3]);
+            const uint32_t ra = down2(lo2(p[0], p[1]), hi2(p[0], p[1]), lo2(p[1], p[2]), hi2(p[1], p[2]), w4);
+            const uint32_t rb = down2(w4, hi2(p[2], p[3]), lo2(p[3], p[4]), hi2(p[3], p[4]), lo2(p[4], p[5]));
+            const uint32_t packed = __byte_perm(ra, rb, 0x6420);  // bytes o0, o1, o2, o3
             uint8_t *d = dst + (size_t)oy * dpitch + ox;
             if (ox + 3 < W) {
-                *reinterpret_cast<uint32_t *>(d) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+                *reinterpret_cast<uint32_t *>(d) = packed;
             } else {
-                for (int q = 0; q < 4 && ox + q < W; ++q) d[q] = (uint8_t)o[q];
+                for (int q = 0; q < 4 && ox + q < W; ++q) d[q] = (uint8_t)(packed >> (8 * q));
             }
         }
     }
@@ -319,8 +385,10 @@ struct PyrTileRef {
     int ix0, iy0;
 };
 
+// Six CTAs per SM (at most 40 registers a thread, no spills with the packed
+// Scharr and horizontal passes): more tiles' loads in flight per SM.
 template <int GT>
-__global__ void __launch_bounds__(PD_THREADS) k_pyr_batch(const uint8_t *tab, int l) {
+__global__ void __launch_bounds__(PD_THREADS, 6) k_pyr_batch(const uint8_t *tab, int l) {
     __shared__ __align__(16) uint8_t s_in[PD_IH][PD_IW];
     __shared__ uint16_t s_v[PD_TH][PD_VW];
     __shared__ BLvlJob s_jobs[kJobsInSmem];

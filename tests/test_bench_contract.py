@@ -81,3 +81,29 @@ def test_cpu_baseline_uses_stream_levels_and_counts_iterations():
     il = r["iters_per_level"]
     assert sorted(il) == [f"L{lv}" for lv in range(specs[0].levels)]
     assert all(v > 0 for v in il.values())
+
+
+@pytest.mark.gpu
+def test_served_sweep_rows():
+    """The bench's served section on a small mix: each rate runs both arms on
+    several traces; the row's p99 is the median of the runs' p99s."""
+    import statistics
+    from types import SimpleNamespace
+
+    import bench
+    import paper_2607_01757_gb300 as vt
+
+    wl = bench.make_workload(6, 3, 11, 1)
+    a = SimpleNamespace(served_requests=120, served_sweep_requests=60, served_reps=3, served_rates=[1.0, 4.0],
+                        served_budget_gb=20.0, served_slots=2, seed=11, frames=3)
+    same = lambda x: x  # noqa: E731 - one rank
+    out = bench.run_served(a, wl, vt.KltParams(), lambda: None, same, same)
+    assert [r["rate_x"] for r in out["sweep"]] == [1.0, 4.0]
+    for row in out["sweep"]:
+        for arm in ("batched", "plain"):
+            r = row[arm]
+            assert len(r["p99_ms_runs"]) == 3 and r["requests"] == 180
+            assert abs(r["p99_ms"] - statistics.median(r["p99_ms_runs"])) < 1e-3
+            assert r["features_per_s"] > 0 and r["p50_ms"] <= r["p99_ms"] + 1e-9
+    assert out["batched_saturated"]["requests"] == 120 and out["plain_saturated"]["requests"] == 120
+    assert set(out["best_at_p99_le_2ms"]) == {"batched", "plain"}
