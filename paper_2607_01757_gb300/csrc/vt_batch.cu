@@ -225,14 +225,16 @@ namespace vt {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tasks, int &off_prefix, int &off_gates,
-                   int &off_gprefix, size_t &bytes) {
+static void layout(int F, int T, int &off_frames, int &off_jobs, int &off_tsrc, int &off_tasks, int &off_prefix,
+                   int &off_gates, int &off_gprefix, size_t &bytes) {
     size_t o = align_up(sizeof(BatchHdr), 64);
     off_frames = (int)o;
     o = align_up(o + sizeof(BFrame) * F, 64);
     off_jobs = (int)o;
     // VT_MAX_LEVELS - 1 tiled lists of F jobs, then the tail list of up to 8 bands per frame
     o = align_up(o + sizeof(BLvlJob) * (size_t)F * (VT_MAX_LEVELS - 1 + 8), 64);
+    off_tsrc = (int)o;
+    o = align_up(o + sizeof(BTileSrc) * (size_t)F * (VT_MAX_LEVELS - 1), 64);
     off_tasks = (int)o;
     o = align_up(o + sizeof(BTask) * T, 64);
     off_prefix = (int)o;
@@ -290,8 +292,8 @@ vt_status vt_batch_create(int max_frames, int max_tasks, vt_batch **out) {
     if (!b) return VT_ERR_OOM;
     b->cap_frames = max_frames > 0 ? max_frames : 1;
     b->cap_tasks = max_tasks > 0 ? max_tasks : 1;
-    int of, oj, ot, op, og, ogp;
-    layout(b->cap_frames, b->cap_tasks, of, oj, ot, op, og, ogp, b->tab_bytes);
+    int of, oj, ots, ot, op, og, ogp;
+    layout(b->cap_frames, b->cap_tasks, of, oj, ots, ot, op, og, ogp, b->tab_bytes);
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
         ok = ok && cudaMallocHost((void **)&b->host[k], b->tab_bytes) == cudaSuccess;
@@ -384,8 +386,8 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     BatchHdr *H = reinterpret_cast<BatchHdr *>(tab);
     memset(H, 0, sizeof(BatchHdr));
     size_t bytes;
-    layout(b->cap_frames, b->cap_tasks, H->off_frames, H->off_jobs, H->off_tasks, H->off_prefix, H->off_gates,
-           H->off_gprefix, bytes);
+    layout(b->cap_frames, b->cap_tasks, H->off_frames, H->off_jobs, H->off_tsrc, H->off_tasks, H->off_prefix,
+           H->off_gates, H->off_gprefix, bytes);
     H->cap_frames = b->cap_frames;
     H->cap_tasks = b->cap_tasks;
     H->nframes = nframes;
@@ -399,6 +401,7 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
     H->P.fp64 = fp64_needed(prm->min_eig);
     BFrame *bf = reinterpret_cast<BFrame *>(tab + H->off_frames);
     BLvlJob *jobs = reinterpret_cast<BLvlJob *>(tab + H->off_jobs);
+    BTileSrc *tsrc = reinterpret_cast<BTileSrc *>(tab + H->off_tsrc);
     int maxL = 1, maxC = 0;
     for (int f = 0; f < nframes; ++f) {
         const vt_frame_job &fj = frames[f];
@@ -427,6 +430,22 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
                 lj[nj].tiles_x = tx;
                 lj[nj].tile0 = tiles;
                 lj[nj].aux = c;
+                BTileSrc &ts = tsrc[(size_t)l * b->cap_frames + nj];
+                const Level &S = p->lv[l], &D = p->lv[l + 1];
+                ts.src = l == 0 ? frames[f].img : S.img;
+                ts.spitch = l == 0 ? frames[f].pitch : S.pitch;
+                ts.vec_ok = l == 0 ? bf[f].vec_ok : 1;
+                ts.w = S.w;
+                ts.h = S.h;
+                ts.dst = D.img;
+                ts.dpitch = D.pitch;
+                ts.grad = S.grad;
+                ts.gpitch = S.gpitch;
+                // level 0 also writes the pyramid's own level-0 copy, unless
+                // the frame is built in place (its image is that level)
+                ts.copy = (l == 0 && frames[f].img != S.img) ? S.img : nullptr;
+                ts.cpitch = S.pitch;
+                ts.tiles_x = tx;
                 tiles += nt;
                 ++nj;
             } else {

@@ -145,6 +145,18 @@ struct BFrame {
     int pad;
 };
 
+// Everything a tile of one tiled pyramid job needs, resolved on the host
+// when the tables are staged (no dependent loads of frame and level tables
+// in the kernel): source level, destination level, gradient planes of the
+// source level, and the level-0 copy destination (null when built in place).
+struct __align__(16) BTileSrc {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint32_t *grad;
+    uint8_t *copy;
+    int w, h, spitch, dpitch, gpitch, cpitch, vec_ok, tiles_x;
+};
+
 struct BLvlJob {
     int frame;
     int tiles_x;
@@ -187,6 +199,7 @@ struct BatchHdr {
     int cap_frames, cap_tasks;
     int off_frames, off_jobs, off_tasks, off_prefix;
     int ngates, gate_points, off_gates, off_gprefix;
+    int off_tsrc, pad_tsrc;  // BTileSrc per tiled job: VT_MAX_LEVELS - 1 lists of cap_frames
     vt_gate_params G;
     KParams P;
 };

@@ -374,16 +374,11 @@ __device__ __forceinline__ int find_job(const BLvlJob *jobs, int n, int t) {
 // level l for every frame of the batch whose tail starts above l (no Scharr
 // planes for GT = VT_GRAD_NONE: the tracker computes gradients itself).  Level 0
 // reads the caller's image and writes the pyramid's level-0 copy from the
-// same tile.  The job list is first copied to shared memory so the per-tile
-// job search does not chain global loads.
+// same tile (unless the frame is built in place).  The job list is first
+// copied to shared memory so the per-tile job search does not chain global
+// loads, and each job's source and destination are resolved on the host
+// (BTileSrc), one load per tile, fetched a tile ahead.
 constexpr int kJobsInSmem = 256;
-
-struct PyrTileRef {
-    const uint8_t *src;
-    int w, h, pitch;
-    bool vec_ok;
-    int ix0, iy0;
-};
 
 // Six CTAs per SM (at most 40 registers a thread, no spills with the packed
 // Scharr and horizontal passes): more tiles' loads in flight per SM.
@@ -395,7 +390,6 @@ __global__ void __launch_bounds__(PD_THREADS, 6) k_pyr_batch(const uint8_t *tab,
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const int njobs = H->njobs[l], tiles = H->ntiles[l];
     if ((int)blockIdx.x >= tiles) return;
-    const BFrame *frames = reinterpret_cast<const BFrame *>(tab + H->off_frames);
     const BLvlJob *gjobs = reinterpret_cast<const BLvlJob *>(tab + H->off_jobs) + (size_t)l * H->cap_frames;
     const bool in_smem = njobs <= kJobsInSmem;
     if (in_smem) {
@@ -403,35 +397,31 @@ __global__ void __launch_bounds__(PD_THREADS, 6) k_pyr_batch(const uint8_t *tab,
         __syncthreads();
     }
     const BLvlJob *jobs = in_smem ? s_jobs : gjobs;
-    // where tile t's input lives, and its frame and tile coordinates
-    auto locate = [&](int t, PyrTileRef &r, BFrame &fr, int &tx, int &ty) {
-        const BLvlJob jb = jobs[find_job(jobs, njobs, t)];
-        fr = frames[jb.frame];
-        const Level src = fr.lv[l];
-        const int tt = t - jb.tile0;
-        ty = tt / jb.tiles_x;
-        tx = tt - ty * jb.tiles_x;
-        r.src = l == 0 ? fr.img : src.img;
-        r.pitch = l == 0 ? fr.pitch : src.pitch;
-        r.vec_ok = l == 0 ? fr.vec_ok != 0 : true;
-        r.w = src.w;
-        r.h = src.h;
-        r.ix0 = 2 * tx * PD_TW - 16;
-        r.iy0 = 2 * ty * PD_TH - 2;
+    const BTileSrc *tsrc = reinterpret_cast<const BTileSrc *>(tab + H->off_tsrc) + (size_t)l * H->cap_frames;
+    // One thread resolves the CTA's next tile (its job's source record and
+    // tile coordinates) into the other slot while the current tile is
+    // computed, so no tile waits for the job search and the record's load.
+    __shared__ BTileSrc s_ts[2];
+    __shared__ int s_txy[2][2];
+    auto locate = [&](int t, int k) {
+        const int j = find_job(jobs, njobs, t);
+        const int tt = t - jobs[j].tile0, nx = jobs[j].tiles_x;
+        s_ts[k] = tsrc[j];
+        s_txy[k][1] = tt / nx;
+        s_txy[k][0] = tt - (tt / nx) * nx;
     };
+    if (threadIdx.x == 0) locate(blockIdx.x, 0);  // the tables are complete before the first launch
+    __syncthreads();
     pdl_wait();  // level l is the previous launch's output
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    int k = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, k ^= 1) {
         if (t + (int)gridDim.x >= tiles) pdl_trigger();  // this CTA's last tile: the next launch may start
-        PyrTileRef r;
-        BFrame fr;
-        int tx, ty;
-        locate(t, r, fr, tx, ty);
-        const Level src = fr.lv[l], dst = fr.lv[l + 1];
-        // level 0 also writes the pyramid's own level-0 copy, unless the
-        // frame was built in place (the caller's image is that level)
-        uint8_t *copy = (l == 0 && r.src != src.img) ? src.img : nullptr;
-        pyr_tile<GT != VT_GRAD_NONE, GT>(r.src, src.w, src.h, r.pitch, r.vec_ok, dst.img, dst.pitch, src.grad,
-                                         src.gpitch, copy, src.pitch, tx, ty, s_in, s_v);
+        const BTileSrc &ts = s_ts[k];  // fields read from shared memory where used
+        const int tx = s_txy[k][0], ty = s_txy[k][1];
+        // slot k ^ 1 was last read before the previous tile's closing barrier
+        if (threadIdx.x == PD_THREADS - 32 && t + (int)gridDim.x < tiles) locate(t + (int)gridDim.x, k ^ 1);
+        pyr_tile<GT != VT_GRAD_NONE, GT>(ts.src, ts.w, ts.h, ts.spitch, ts.vec_ok != 0, ts.dst, ts.dpitch, ts.grad,
+                                         ts.gpitch, ts.copy, ts.cpitch, tx, ty, s_in, s_v);
         __syncthreads();
     }
 }
