@@ -33,6 +33,9 @@ if ROOT not in sys.path:
 
 METRIC = "tracked features/s & p99 frame latency, batched/served vs plain KLT, 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
+# upload slots of the end-to-end run: step t's frames land in slot t % 3 while
+# step t-1's slot (level 0 of the previous pyramids) is still read by step t
+E2E_SLOTS = 3
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
@@ -262,47 +265,80 @@ def run_native(a, rank, world, local_rank):
     gprm = vt.GateParams(min_disp=1.0, z_min=0.1, z_max=50.0, max_reproj=1.5)
     rigs = [vt.StereoRig(*synth.stream_rig(sp)) if sp.stereo else None for sp in specs]
     grad_type = {"s16": vt.VT_GRAD_S16, "f16": vt.VT_GRAD_F16, "none": vt.VT_GRAD_NONE}[a.grad]
-    tr = BatchedTracker(specs, prm, grad_type=grad_type, gate=gprm, rigs=rigs)
     S = len(specs)
     sids = list(range(S))
-    # device frame store: frames and keypoints of every stream
-    left = [[torch.from_numpy(fr.left[k]).to(dev) for k in range(F)] for fr in frames]
-    right = [[torch.from_numpy(fr.right[k]).to(dev) if fr.right[k] is not None else None for k in range(F)]
-             for fr in frames]
+    # Input ring of every stream: the F frames of the device frame store
+    # (slots 0 .. F-1), then E2E_SLOTS upload slots for the end-to-end run,
+    # views into packed device buffers that one H2D copy per step fills.
+    # Each slot is level 0 of its own pyramid (vt_pyramid_create_on), so a
+    # frame is never copied into a pyramid: it lands in its slot and the
+    # batched run builds the upper levels and the gradients from it.
+    pitch16 = lambda w: (w + 15) // 16 * 16  # noqa: E731
+
+    def slot_buffer(img):
+        h, w = img.shape
+        buf = torch.zeros(pitch16(w) * h + 64, dtype=torch.uint8, device=dev)  # 32+ readable bytes after the last row
+        view = buf[:pitch16(w) * h].view(h, pitch16(w))[:, :w]
+        view.copy_(torch.from_numpy(img))
+        return view
+
+    left = [[slot_buffer(fr.left[k]) for k in range(F)] for fr in frames]
+    right = [[slot_buffer(fr.right[k]) if fr.right[k] is not None else None for k in range(F)] for fr in frames]
     kps = [[torch.from_numpy(fr.kps[k]).to(dev) for k in range(F)] for fr in frames]
     nkp = [[int(fr.kps[k].shape[0]) for k in range(F)] for fr in frames]
+    # packed upload buffers of the end-to-end run (one region per image, rows of pitch16(w))
+    off_l, off_r, img_bytes = [], [], 0
+    for sp in specs:
+        off_l.append(img_bytes)
+        img_bytes += pitch16(sp.w) * sp.h
+        if sp.stereo:
+            off_r.append(img_bytes)
+            img_bytes += pitch16(sp.w) * sp.h
+        else:
+            off_r.append(None)
+    n_up = 0 if a.no_e2e else E2E_SLOTS
+    dev_img = [torch.zeros(img_bytes + 64, dtype=torch.uint8, device=dev) for _ in range(n_up)]
+
+    def up_view(k, off, sp):
+        return dev_img[k][off:off + pitch16(sp.w) * sp.h].view(sp.h, pitch16(sp.w))[:, :sp.w]
+
+    ring = [([left[i][f] for f in range(F)] + [up_view(k, off_l[i], sp) for k in range(n_up)],
+             ([right[i][f] for f in range(F)] + [up_view(k, off_r[i], sp) for k in range(n_up)]) if sp.stereo
+             else None) for i, sp in enumerate(specs)]
+    tr = BatchedTracker(specs, prm, grad_type=grad_type, gate=gprm, rigs=rigs, ring=ring)
+    last_slot = [0]  # ring slot built by the latest step (every stream alike)
 
     def step_args(t):
         fp, fc = pingpong(t - 1, F), pingpong(t, F)
-        L = [left[i][fc] for i in sids]
-        R = [right[i][fc] for i in sids]
         kt = [kps[i][fp] for i in sids]
         ks = [kps[i][fc] for i in sids]
         n_t = [nkp[i][fp] if t > 0 else 0 for i in sids]
         n_s = [nkp[i][fc] for i in sids]
-        return L, R, kt, ks, n_t, n_s
+        return [(last_slot[0], fc)] * S, kt, ks, n_t, n_s
 
-    features = lambda t: sum(step_args(t)[4])  # noqa: E731
+    features = lambda t: sum(step_args(t)[3])  # noqa: E731
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def batched_prepare(t, flops=None, gate=False):
         # host-only: job tables of step t into the pinned staging buffer
-        L, R, kt, ks, n_t, n_s = step_args(t)
-        tr.stage(tr.step_tables(sids, n_t, n_s, L, R, flops=flops, kpt=kt, kps=ks, gate=gate))
+        ri, kt, ks, n_t, n_s = step_args(t)
+        tr.stage(tr.step_tables(sids, n_t, n_s, flops=flops, kpt=kt, kps=ks, gate=gate, ring_idx=ri))
 
     def batched_launch(t, events=None, graph=True):
         tr.run(stream, graph=graph, events=events)
         tr.advance(sids)
+        last_slot[0] = pingpong(t, F)
 
     def batched_step(t, events=None, graph=True, flops=None, gate=False):
         batched_prepare(t, flops, gate)
         batched_launch(t, events, graph)
 
     def plain_step(t):
-        L, R, kt, ks, n_t, n_s = step_args(t)
-        tr.plain_step(sids, n_t, n_s, L, R, stream, kpt=kt, kps=ks, gate=False)
+        ri, kt, ks, n_t, n_s = step_args(t)
+        tr.plain_step(sids, n_t, n_s, stream=stream, kpt=kt, kps=ks, gate=False, ring_idx=ri)
         tr.advance(sids)
+        last_slot[0] = pingpong(t, F)
 
     def timed(fn, t0, K, prepare=None, flush_between=True):
         """Per-step device time (CUDA events on the launching stream).  The
@@ -412,7 +448,7 @@ def run_native(a, rank, world, local_rank):
         fl = [(torch.zeros(max(1, s.n_max), dtype=torch.int32, device=dev),
                torch.zeros(max(1, s.n_max), dtype=torch.int32, device=dev)) for s in tr.streams]
         batched_step(t, graph=False, flops=fl)
-        _, _, _, _, n_t, n_s = step_args(t)
+        _, _, _, n_t, n_s = step_args(t)
         torch.cuda.synchronize()
         tot = 0
         for k, s in enumerate(tr.streams):
@@ -465,7 +501,7 @@ def run_native(a, rank, world, local_rank):
             torch.cuda.synchronize()
             gsteps.append(e[0].elapsed_time(e_end))
             gate_ms.append(e[3].elapsed_time(e_end))
-            _, _, _, _, n_t_, n_s_ = step_args(t)
+            _, _, _, n_t_, n_s_ = step_args(t)
             for k, s in enumerate(tr.streams):
                 if s.rig is not None and n_s_[k] > 0:
                     pairs += n_s_[k]
@@ -491,7 +527,7 @@ def run_native(a, rank, world, local_rank):
         carry_ms, spawn_ms, kept_n, surv_n, spawned_n = [], [], 0, 0, 0
         for i in range(a.steps):
             batched_step(t)  # tracking of the previous frame's keypoints (their temporal status)
-            _, _, kt_, ks_, n_t_, n_s_ = step_args(t)
+            _, kt_, ks_, n_t_, n_s_ = step_args(t)
             for k, s in enumerate(tr.streams):  # pools = the previous keypoints, ages 1..5
                 n = n_t_[k]
                 if n not in idx_cache:
@@ -567,7 +603,7 @@ def run_native(a, rank, world, local_rank):
         barrier()
         t += a.steps
         ptot = max_over_ranks(sum(pms))
-        L_, R_, kt_, ks_, n_t_, n_s_ = step_args(t)
+        _, kt_, ks_, n_t_, n_s_ = step_args(t)
         plain = {"value": sum_over_ranks(pfeats) / (ptot / 1e3), "ms_per_step": ptot / a.steps,
                  "p50_ms": float(np.percentile(pms, 50)), "p99_ms": float(np.percentile(pms, 99)),
                  "gpu_launches_per_step": tr.plain_launches(sids, n_t_, n_s_, gate=False)}
@@ -577,86 +613,78 @@ def run_native(a, rank, world, local_rank):
     # in one copy per step (all streams' images packed, 16-byte aligned), the
     # batched run follows on the compute stream, and the step's results (all
     # streams' points and status, contiguous) come back in two copies.  The copy
-    # of step t+1 runs on a second stream while step t computes (two device
-    # slots); the wall clock covers all K steps until the last results are on
-    # the host.  A synchronous variant (one step at a time) gives the latency.
+    # of step t+1 runs on a second stream while step t computes (three upload
+    # slots, each level 0 of its pyramids: the frames are never copied again);
+    # the wall clock covers all K steps until the last results are on the
+    # host.  A synchronous variant (one step at a time) gives the latency.
     e2e = None
     if not a.no_e2e:
-        align = lambda v: (v + 15) // 16 * 16  # noqa: E731
-        off_l, off_r, off = [], [], 0
-        for s in tr.streams:
-            off_l.append(off)
-            off = align(off + s.w * s.h)
-            if s.stereo:
-                off_r.append(off)
-                off = align(off + s.w * s.h)
-            else:
-                off_r.append(None)
-        img_bytes = off
         kp_off, kq = [], 0
         for i, s in enumerate(tr.streams):
             kp_off.append(kq)
             kq += max(nkp[i]) * 2
-        host_img = [torch.empty(img_bytes, dtype=torch.uint8).pin_memory() for _ in range(F)]
+        # pinned host frames packed like the upload buffers (rows of pitch16(w))
+        host_img = [torch.zeros(img_bytes, dtype=torch.uint8).pin_memory() for _ in range(F)]
         host_kp = [torch.zeros(kq, dtype=torch.float32).pin_memory() for _ in range(F)]
         for f in range(F):
-            for i, (s, fr) in enumerate(zip(tr.streams, frames)):
-                host_img[f][off_l[i]:off_l[i] + s.w * s.h].copy_(torch.from_numpy(fr.left[f]).reshape(-1))
-                if s.stereo:
-                    host_img[f][off_r[i]:off_r[i] + s.w * s.h].copy_(torch.from_numpy(fr.right[f]).reshape(-1))
+            for i, (sp, fr) in enumerate(zip(specs, frames)):
+                pv = lambda off: host_img[f][off:off + pitch16(sp.w) * sp.h].view(sp.h, pitch16(sp.w))[:, :sp.w]  # noqa: E731
+                pv(off_l[i]).copy_(torch.from_numpy(fr.left[f]))
+                if sp.stereo:
+                    pv(off_r[i]).copy_(torch.from_numpy(fr.right[f]))
                 host_kp[f][kp_off[i]:kp_off[i] + 2 * nkp[i][f]].copy_(torch.from_numpy(fr.kps[f]).reshape(-1))
-        dev_img = [torch.empty(img_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
-        dev_kp = [torch.empty((2, kq), dtype=torch.float32, device=dev) for _ in range(2)]
-        host_pts = [torch.empty_like(tr.out_pts, device="cpu").pin_memory() for _ in range(2)]
-        host_st = [torch.empty_like(tr.out_st, device="cpu").pin_memory() for _ in range(2)]
+        dev_kp = [torch.empty((2, kq), dtype=torch.float32, device=dev) for _ in range(E2E_SLOTS)]
+        host_pts = [torch.empty_like(tr.out_pts, device="cpu").pin_memory() for _ in range(E2E_SLOTS)]
+        host_st = [torch.empty_like(tr.out_st, device="cpu").pin_memory() for _ in range(E2E_SLOTS)]
         copy_stream = torch.cuda.Stream()
-        h2d_done = [torch.cuda.Event() for _ in range(2)]
-        run_start = [torch.cuda.Event() for _ in range(2)]
+        h2d_done = [torch.cuda.Event() for _ in range(E2E_SLOTS)]
+        run_start = [torch.cuda.Event() for _ in range(E2E_SLOTS)]
         h2d_b = img_bytes + 2 * kq * 4
         d2h_b = tr.out_pts.numel() * 4 + tr.out_st.numel()
         table_cache = {}
 
-        def e2e_copy(t_, slot):
-            # step t_'s inputs into device slot `slot` (copy stream)
+        def e2e_copy(t_):
+            # step t_'s inputs into upload slot t_ % E2E_SLOTS (copy stream)
+            k = t_ % E2E_SLOTS
             fp, fc = pingpong(t_ - 1, F), pingpong(t_, F)
-            dev_img[slot].copy_(host_img[fc], non_blocking=True)
-            dev_kp[slot][0].copy_(host_kp[fp], non_blocking=True)
-            dev_kp[slot][1].copy_(host_kp[fc], non_blocking=True)
-            h2d_done[slot].record(copy_stream)
+            dev_img[k][:img_bytes].copy_(host_img[fc], non_blocking=True)
+            dev_kp[k][0].copy_(host_kp[fp], non_blocking=True)
+            dev_kp[k][1].copy_(host_kp[fc], non_blocking=True)
+            h2d_done[k].record(copy_stream)
 
-        def e2e_submit(t_, slot, prefetch=True, t1=None):
-            """Run step t_ from slot `slot` (its inputs copied by the previous
-            call); with prefetch, step t_+1's copy starts with this run, so it
-            overlaps the pyramid launches and not the L2-sensitive tracking."""
+        def e2e_submit(t_, prefetch=True):
+            """Run step t_ from its upload slot (copied by the previous call);
+            with prefetch, step t_+1's copy starts with this run, so it
+            overlaps the pyramid launches and not the L2-sensitive tracking.
+            Slot t_+1 was read last by steps t_-2 (current) and t_-1
+            (previous), both finished when this run starts."""
+            k = t_ % E2E_SLOTS
             fp, fc = pingpong(t_ - 1, F), pingpong(t_, F)
-            stream.wait_event(h2d_done[slot])
-            run_start[slot].record(stream)
+            stream.wait_event(h2d_done[k])
+            run_start[k].record(stream)
             if prefetch:
                 with torch.cuda.stream(copy_stream):
-                    copy_stream.wait_event(run_start[slot])  # slot 1 - slot's previous run has finished too
-                    e2e_copy(t_ + 1, 1 - slot)
-            key = (slot, fp, fc, tr.streams[0].built % 2)  # the tables only depend on these
+                    copy_stream.wait_event(run_start[k])
+                    e2e_copy(t_ + 1)
+            key = (last_slot[0], k, fp, fc)  # the tables only depend on these
             if key not in table_cache:
-                L = [dev_img[slot][off_l[i]:off_l[i] + s.w * s.h].view(s.h, s.w) for i, s in enumerate(tr.streams)]
-                R = [dev_img[slot][off_r[i]:off_r[i] + s.w * s.h].view(s.h, s.w) if s.stereo else None
-                     for i, s in enumerate(tr.streams)]
-                kt = [dev_kp[slot][0][kp_off[i]:kp_off[i] + 2 * nkp[i][fp]].view(-1, 2) for i in sids]
-                ks = [dev_kp[slot][1][kp_off[i]:kp_off[i] + 2 * nkp[i][fc]].view(-1, 2) for i in sids]
+                kt = [dev_kp[k][0][kp_off[i]:kp_off[i] + 2 * nkp[i][fp]].view(-1, 2) for i in sids]
+                ks = [dev_kp[k][1][kp_off[i]:kp_off[i] + 2 * nkp[i][fc]].view(-1, 2) for i in sids]
                 n_t = [nkp[i][fp] for i in sids]
                 n_s = [nkp[i][fc] for i in sids]
-                table_cache[key] = tr.step_tables(sids, n_t, n_s, L, R, kpt=kt, kps=ks, gate=False)
+                table_cache[key] = tr.step_tables(sids, n_t, n_s, kpt=kt, kps=ks, gate=False,
+                                                  ring_idx=[(last_slot[0], F + k)] * S)
             tr.stage(table_cache[key])
             tr.run(stream, graph=True)
             tr.advance(sids)
-            host_pts[slot].copy_(tr.out_pts, non_blocking=True)
-            host_st[slot].copy_(tr.out_st, non_blocking=True)
-            if t1 is not None:
-                t1.record(stream)
+            last_slot[0] = F + k
+            host_pts[k].copy_(tr.out_pts, non_blocking=True)
+            host_st[k].copy_(tr.out_st, non_blocking=True)
 
         with torch.cuda.stream(copy_stream):
-            e2e_copy(t, t % 2)
+            e2e_copy(t)
         for _ in range(a.warmup):
-            e2e_submit(t, t % 2)
+            e2e_submit(t)
             t += 1
         torch.cuda.synchronize()
         barrier()
@@ -664,7 +692,7 @@ def run_native(a, rank, world, local_rank):
         efeats = 0
         w0 = time.perf_counter()
         for i in range(a.steps):  # K runs, K copies (the last one feeds the next section)
-            e2e_submit(t, t % 2)
+            e2e_submit(t)
             efeats += features(t)
             t += 1
         torch.cuda.synchronize()  # every step's results are on the host
@@ -675,8 +703,8 @@ def run_native(a, rank, world, local_rank):
         for i in range(a.steps):
             w1 = time.perf_counter()
             with torch.cuda.stream(copy_stream):
-                e2e_copy(t, t % 2)
-            e2e_submit(t, t % 2, prefetch=False)
+                e2e_copy(t)
+            e2e_submit(t, prefetch=False)
             torch.cuda.synchronize()
             sms.append((time.perf_counter() - w1) * 1e3)
             t += 1
@@ -729,6 +757,8 @@ def run_native(a, rank, world, local_rank):
             "stereo_streams": sum(1 for s in specs if s.stereo),
             "features_per_step": feats // a.steps,
             "frames_per_stream": F,
+            "level0": "input ring: each frame sits in a ring slot that is level 0 of its pyramid "
+                      "(vt_pyramid_create_on); no frame is copied into a pyramid",
             "gradients": {"s16": "stored int16 Scharr planes", "f16": "stored half Scharr planes",
                           "none": "computed inside the tracker (bit-identical to int16)"}[a.grad],
             "win": prm.win, "levels": "per stream (4-6)", "max_iters": prm.max_iters, "eps": prm.eps,
@@ -918,24 +948,28 @@ def pyramid_launch_bytes(streams, grad, vt):
     l = 0), writes level l+1 and, with gradients, 4 B/px of level l's planes;
     the tail reads the frame's first tail level c and writes every smaller
     level and the planes of c and below.  Level 0 also writes the pyramid's
-    level-0 copy unless the frame is built in place."""
+    level-0 copy unless the frame is built in place (a ring stream: its
+    frames land in level 0).  c is the first level whose rows (at the
+    pyramid's pitch) fit in 40 KB."""
     tail_max = 40960
     per = {}
     for s in streams:
+        in_place = bool(getattr(s, "ring_left", None))
         dims, w, h = [], s.w, s.h
         for _ in range(s.levels):
             dims.append((w, h))
             w, h = (w + 1) // 2, (h + 1) // 2
-        c = next((l for l, (lw, lh) in enumerate(dims) if ((lw + 63) // 64 * 64) * lh <= tail_max), len(dims) - 1)
+        pitch = [vt.vt_pyramid_level(s.pyr[0], l)[3] for l in range(s.levels)]
+        c = next((l for l, (lw, lh) in enumerate(dims) if pitch[l] * lh <= tail_max), len(dims) - 1)
         gb = 4 if grad else 0
         for _ in range(2 if s.stereo else 1):
             for l in range(c):
                 lw, lh = dims[l]
                 b = lw * lh + dims[l + 1][0] * dims[l + 1][1] + gb * lw * lh
-                if l == 0 and not getattr(s, "in_place", False):
+                if l == 0 and not in_place:
                     b += lw * lh
                 per[l] = per.get(l, 0) + b
-            b = dims[c][0] * dims[c][1] * (2 if c == 0 and not getattr(s, "in_place", False) else 1)
+            b = dims[c][0] * dims[c][1] * (2 if c == 0 and not in_place else 1)
             for l in range(c, len(dims)):
                 b += gb * dims[l][0] * dims[l][1] + (dims[l][0] * dims[l][1] if l > c else 0)
             per["tail"] = per.get("tail", 0) + b

@@ -127,6 +127,30 @@ VT_API vt_status vt_pyramid_build_grad(const uint8_t *img, int w, int h, int pit
 VT_API vt_status vt_pyramid_create(int w, int h, int levels, vt_pyramid **out);
 
 /*
+ * vt_pyramid_create_on - like vt_pyramid_create, but level 0 of the pyramid
+ * is the caller's device buffer `level0` (h rows of `pitch` bytes, row y at
+ * level0 + y * pitch) instead of library memory: a frame that lands there
+ * (a camera or host upload, one slot of an input ring) is level 0 as it is,
+ * and a build or batched run that names `level0` as its image builds the
+ * upper levels and the Scharr planes from it without copying it
+ * (Sec. IV: the pyramids are built from the incoming frames).
+ *
+ * Ownership: the buffer stays the caller's; the library never frees it
+ * (vt_pyramid_free releases only the levels above 0 and the planes).  The
+ * caller keeps it allocated, and leaves it unchanged while queued builds or
+ * tracking calls read it.  A build from another image, or vt_pyramid_upload,
+ * writes that image into the caller's buffer.
+ *
+ * Layout rules (VT_ERR_ARG otherwise): level0 16-byte aligned, pitch a
+ * multiple of 16 and >= w, and level0_bytes >= pitch * h + 32: the tracking
+ * kernels stage windows in whole aligned 16-byte chunks, which may read up
+ * to 31 bytes past a row's last pixel (contents unused).  Other arguments as
+ * vt_pyramid_create.  Synchronous.
+ */
+VT_API vt_status vt_pyramid_create_on(const uint8_t *level0, int pitch, size_t level0_bytes, int w, int h,
+                                      int levels, vt_pyramid **out);
+
+/*
  * vt_pyramid_upload - copy a w x h frame (`pitch` bytes per row; host memory,
  * pinned for an asynchronous copy, or device memory with img_on_device = 1)
  * into level 0 of `p` on `cuda_stream` (one 2-D memory copy, no kernel), so

@@ -274,10 +274,11 @@ __device__ __forceinline__ void stage_window_otf(const Level &L, int x0, int y0,
 // samples (KRuns): T and its gradients, zero for samples outside the
 // window.  The (win + 1)^2 image and gradient footprint is first staged in
 // shared memory (16-byte cp.async chunks of each clamped row when the
-// columns lie inside the level -- they may read up to 26 image bytes and 24
-// gradient bytes past a row's last pixel, inside the pitch or the pyramid
-// allocation's slack -- else one clamped column per lane; computed in place
-// for a level without gradient planes).
+// columns lie inside the level -- they may read up to 26 image bytes (window
+// 21; at most 30 for any window) and 24 gradient bytes past a row's last
+// pixel, inside the pitch, the pyramid allocation's slack, or the 32 bytes a
+// caller-owned level 0 keeps readable after its last row -- else one clamped
+// column per lane; computed in place for a level without gradient planes).
 template <int WIN, int GT>
 __device__ __forceinline__ void load_template(const Level &L, float ux, float uy, int lane,
                                               float (&T)[KRuns<WIN>::NS], float (&GX)[KRuns<WIN>::NS],
@@ -364,7 +365,8 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
 // its columns lie inside the image, each (clamped) row is copied in whole
 // aligned 16-byte chunks by cp.async (global to shared, no register round
 // trip); they may read up to 26 bytes (window 21) past a row's last pixel,
-// inside the level's pitch or the pyramid allocation's slack.  Otherwise lane
+// inside the level's pitch, the pyramid allocation's slack or a caller-owned
+// level 0's 32 readable bytes after its last row.  Otherwise lane
 // c loads column c (clamped) of every row.  Returns the byte offset of column
 // 0 within a staged row.
 template <int WIN>

@@ -683,7 +683,10 @@ vt_status launch_scharr(const GradJobs &jobs, int total_blocks, int gtype, cudaS
 }
 
 // ------------------------------------------------------------------ host side
-static vt_status alloc_pyramid(int w, int h, int levels, vt_pyramid **out) {
+// `level0` (nullable): the caller's level-0 buffer (row pitch `pitch0`); the
+// allocation then holds only the levels above 0 and the planes.
+static vt_status alloc_pyramid(int w, int h, int levels, vt_pyramid **out, uint8_t *level0 = nullptr,
+                               int pitch0 = 0) {
     vt_pyramid *p = (vt_pyramid *)calloc(1, sizeof(vt_pyramid));
     if (!p) return VT_ERR_OOM;
     p->w = w;
@@ -698,10 +701,10 @@ static vt_status alloc_pyramid(int w, int h, int levels, vt_pyramid **out) {
         Level &L = p->lv[l];
         L.w = lw;
         L.h = lh;
-        L.pitch = round_up(lw, kImgPitchAlign);
+        L.pitch = (l == 0 && level0) ? pitch0 : round_up(lw, kImgPitchAlign);
         L.gpitch = round_up(lw, kGradPitchAlign);
         img_off[l] = off;
-        off += ((size_t)L.pitch * lh + 255) / 256 * 256;
+        if (l > 0 || !level0) off += ((size_t)L.pitch * lh + 255) / 256 * 256;
         lw = (lw + 1) / 2;
         lh = (lh + 1) / 2;
     }
@@ -717,7 +720,7 @@ static vt_status alloc_pyramid(int w, int h, int levels, vt_pyramid **out) {
     }
     p->bytes = off;
     for (int l = 0; l < levels; ++l) {
-        p->lv[l].img = (uint8_t *)p->base + img_off[l];
+        p->lv[l].img = (l == 0 && level0) ? level0 : (uint8_t *)p->base + img_off[l];
         p->lv[l].grad = (uint32_t *)((uint8_t *)p->base + grad_off[l]);
     }
     static_assert(sizeof(Level) * VT_MAX_LEVELS <= 256, "level table must fit its slot");
@@ -833,6 +836,15 @@ vt_status vt_pyramid_create(int w, int h, int levels, vt_pyramid **out) {
     if (!out || w <= 0 || h <= 0 || levels < 1 || levels > VT_MAX_LEVELS) return VT_ERR_ARG;
     *out = nullptr;
     return alloc_pyramid(w, h, levels, out);
+}
+
+vt_status vt_pyramid_create_on(const uint8_t *level0, int pitch, size_t level0_bytes, int w, int h, int levels,
+                               vt_pyramid **out) {
+    if (!out || !level0 || w <= 0 || h <= 0 || levels < 1 || levels > VT_MAX_LEVELS) return VT_ERR_ARG;
+    if ((uintptr_t)level0 % 16 != 0 || pitch % 16 != 0 || pitch < w) return VT_ERR_ARG;
+    if (level0_bytes < (size_t)pitch * h + 32) return VT_ERR_ARG;
+    *out = nullptr;
+    return alloc_pyramid(w, h, levels, out, const_cast<uint8_t *>(level0), pitch);
 }
 
 vt_status vt_pyramid_level(const vt_pyramid *p, int lvl, const uint8_t **ptr, int *w, int *h, int *pitch) {

@@ -79,6 +79,7 @@ _sig("vt_klt_track_ex", i32, [vp, vp, vp, i32, vp, C.POINTER(vt_klt_params), vp,
 _sig("vt_klt_track_fb", i32, [vp, vp, vp, i32, C.POINTER(vt_klt_params), vp, vp, vp, C.POINTER(vt_klt_diag), vp])
 _sig("vt_fb_check", i32, [vp, vp, vp, vp, i32, f32, vp, vp])
 _sig("vt_pyramid_create", i32, [i32, i32, i32, C.POINTER(vp)])
+_sig("vt_pyramid_create_on", i32, [vp, i32, C.c_size_t, i32, i32, i32, C.POINTER(vp)])
 _sig("vt_status_str", C.c_char_p, [i32])
 _sig("vt_version", C.c_char_p, [])
 
@@ -314,6 +315,26 @@ def vt_pyramid_create(w: int, h: int, levels: int) -> Pyramid:
     hd = vp()
     _check(_lib.vt_pyramid_create(w, h, levels, C.byref(hd)), "vt_pyramid_create")
     return Pyramid(hd.value)
+
+
+def vt_pyramid_create_on(level0, levels: int, nbytes: int | None = None) -> Pyramid:
+    """A pyramid whose level 0 is the caller's device image `level0` (2-D
+    uint8 CUDA tensor, rows 16-byte aligned; usually a view into a larger
+    buffer): builds that name `level0` as their image copy nothing.
+    nbytes: bytes readable from level0's first element (default: to the end
+    of the tensor's storage); at least pitch * h + 32.  The handle keeps a
+    reference to `level0`."""
+    p, w, h, pitch, dev = _img_args(level0)
+    if not dev:
+        raise ValueError("level 0 must be a CUDA tensor")
+    if nbytes is None:
+        st = level0.untyped_storage()
+        nbytes = st.data_ptr() + st.nbytes() - p
+    hd = vp()
+    _check(_lib.vt_pyramid_create_on(p, pitch, int(nbytes), w, h, levels, C.byref(hd)), "vt_pyramid_create_on")
+    pyr = Pyramid(hd.value)
+    pyr.level0 = level0
+    return pyr
 
 
 # ------------------------------------------------------------------ batched

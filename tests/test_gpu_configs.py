@@ -299,3 +299,62 @@ def test_stereo_temporal_sequence_64_frames_pool_aging_batched():
     tr.free()
     assert checked == 2 * F - 1
     assert max_age >= 20, max_age  # some tracks live through a third of the sequence
+
+
+def test_input_ring_equals_input_slots():
+    """A tracker over an input ring (each slot level 0 of its own pyramid,
+    frames never copied) gives bit-identical points, status and errors to the
+    tracker that copies each frame from its input slot, batched and plain."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+    from paper_2607_01757_gb300.engine import BatchedTracker
+
+    specs = synth.make_stream_mix(16, seed=9, kp_range=(150, 400))
+    pick = [sp for sp in specs if sp.stereo][:2] + [sp for sp in specs if not sp.stereo][:1]
+    F = 3
+    frames = [synth.render_stream_frames(sp, F) for sp in pick]
+
+    def slot(img):
+        h, w = img.shape
+        p = (w + 15) // 16 * 16
+        buf = torch.zeros(p * h + 64, dtype=torch.uint8, device="cuda")
+        v = buf[:p * h].view(h, p)[:, :w]
+        v.copy_(torch.from_numpy(img))
+        return v
+
+    ring = [([slot(f.left[k]) for k in range(F)], [slot(f.right[k]) for k in range(F)] if sp.stereo else None)
+            for sp, f in zip(pick, frames)]
+    prm = vt.KltParams()
+    tr_r = BatchedTracker(pick, prm, ring=ring)
+    tr_s = BatchedTracker(pick, prm)
+    sids = list(range(len(pick)))
+    dev = lambda a: torch.from_numpy(a).cuda() if a is not None else None  # noqa: E731
+    kp = [[dev(f.kps[k]) for k in range(F)] for f in frames]
+    for plain in (False, True):
+        for t in range(F):
+            n_t = [len(f.kps[t - 1]) if t > 0 else 0 for f in frames]
+            n_s = [len(f.kps[t]) for f in frames]
+            kt = [kp[i][t - 1] if t > 0 else kp[i][0] for i in sids]
+            ks = [kp[i][t] for i in sids]
+            L = [dev(f.left[t]) for f in frames]
+            R = [dev(f.right[t]) for f in frames]
+            ri = [((t - 1) % F, t)] * len(sids)
+            if plain:
+                tr_r.plain_step(sids, n_t, n_s, kpt=kt, kps=ks, ring_idx=ri)
+                tr_s.plain_step(sids, n_t, n_s, L, R, kpt=kt, kps=ks)
+            else:
+                tr_r.stage(tr_r.step_tables(sids, n_t, n_s, kpt=kt, kps=ks, ring_idx=ri))
+                tr_r.run(graph=True)
+                tr_s.stage(tr_s.step_tables(sids, n_t, n_s, L, R, kpt=kt, kps=ks))
+                tr_s.run(graph=True)
+            tr_r.advance(sids)
+            tr_s.advance(sids)
+            torch.cuda.synchronize()
+            for a, b in ((tr_r.out_pts, tr_s.out_pts), (tr_r.out_st, tr_s.out_st), (tr_r.out_err, tr_s.out_err)):
+                assert torch.equal(a, b), (plain, t)
+            assert int(tr_r.out_st.sum().item()) > 0
+    with pytest.raises(ValueError):  # a ring stream's step names its slots
+        tr_r.step_tables(sids, [0] * 3, [0] * 3)
+    tr_r.free()
+    tr_s.free()

@@ -145,3 +145,67 @@ def test_frame_uploaded_into_level0_builds_in_place(w, h):
     batch.free()
     a.free()
     b.free()
+
+
+@pytest.mark.parametrize("w,h", [(752, 480), (1440, 1080), (97, 65), (16, 3)])
+def test_pyramid_on_caller_level0(w, h):
+    """A pyramid whose level 0 is the caller's buffer (vt_pyramid_create_on):
+    built in place by the single-pair call and by the batched launches, it
+    equals the oracle bit for bit, level 0 stays the caller's frame, tracking
+    against it gives the owned pyramid's results, the buffer outlives the
+    pyramid, and bad layouts are argument errors."""
+    import torch
+
+    import paper_2607_01757_gb300 as vt
+
+    img = _img(w, h, seed=11 * w + h)
+    L = _levels_for(w, h)
+    ref = oracle.build_pyramid(img, L)
+    pitch = (w + 15) // 16 * 16
+
+    def slot():
+        buf = torch.zeros(pitch * h + 64, dtype=torch.uint8, device="cuda")
+        v = buf[:pitch * h].view(h, pitch)[:, :w]
+        v.copy_(torch.from_numpy(img))
+        return v
+
+    va, vb = slot(), slot()
+    a = vt.vt_pyramid_create_on(va, L)
+    b = vt.vt_pyramid_create_on(vb, L)
+    assert a.level(0).data_ptr() == va.data_ptr() and a.level(0).stride(0) == pitch
+    vt.vt_pyramid_build_grad(va, L, vt.VT_GRAD_S16, out=a)
+    batch = vt.Batch(2, 1)
+    vt.vt_batch_set(batch, [vt.frame_job(vb, b)], [], vt.KltParams(levels=L))
+    vt.vt_batch_run(batch)
+    torch.cuda.synchronize()
+    for p in (a, b):
+        for l in range(L):
+            assert np.array_equal(p.level(l).cpu().numpy(), ref.levels[l]), l
+            g = p.grad(l).cpu().numpy()
+            assert np.array_equal(g[..., 0], ref.gx[l]) and np.array_equal(g[..., 1], ref.gy[l]), l
+    if min(w, h) >= 64:  # tracking on the caller-level-0 pyramids equals tracking on owned ones
+        own = vt.vt_pyramid_build_grad(img, L, vt.VT_GRAD_S16)
+        rng = np.random.Generator(np.random.PCG64(w + h))
+        pts = torch.from_numpy(rng.uniform([0, 0], [w - 1, h - 1], (300, 2)).astype(np.float32)).cuda()
+        prm = vt.KltParams(levels=L)
+        outs = []
+        for p0, p1 in ((a, b), (own, own)):
+            o = torch.zeros_like(pts)
+            st = torch.zeros(300, dtype=torch.uint8, device="cuda")
+            vt.vt_klt_track_fb(p0, p1, pts, prm, o, st)
+            torch.cuda.synchronize()
+            outs.append((o.cpu().numpy(), st.cpu().numpy()))
+        assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][0], outs[1][0])
+        own.free()
+    batch.free()
+    a.free()
+    b.free()
+    assert np.array_equal(va.cpu().numpy(), img)  # freeing the pyramid left the caller's buffer alone
+    buf = torch.zeros(pitch * h + 64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(vt.VTError):  # too few readable bytes after the last row
+        vt.vt_pyramid_create_on(buf[:pitch * h].view(h, pitch)[:, :w], L, nbytes=pitch * h + 16)
+    if pitch > 16:
+        with pytest.raises(vt.VTError):  # pitch not a multiple of 16
+            vt.vt_pyramid_create_on(buf[:(pitch - 8) * h].view(h, pitch - 8)[:, :min(w, pitch - 8)], L)
+    with pytest.raises(vt.VTError):  # level 0 not 16-byte aligned
+        vt.vt_pyramid_create_on(buf[8:8 + pitch * h].view(h, pitch)[:, :w], L)
