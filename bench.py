@@ -45,9 +45,9 @@ SM_MAX_MHZ = 2070.0
 # for that workload and only while the sources still hash the same: a kernel
 # changed since the capture reports null.
 NCU_CAPTURES = {
-    "k_klt_batch": {"bytes": 438682112 + 3838208, "date": "2026-12-04", "sources_sha1": "ca75a84b43fd2ab758480c8cf28a553466acbcb1"},
-    "pyramid": {"bytes": 62472448 + 264290304 + 15801344 + 7956992 + 3414784 + 0 + 1630464 + 256,
-                "date": "2026-12-04", "sources_sha1": "0999f480d2be8370202af864d6f447a8e8d58903"},
+    "k_klt_batch": {"bytes": 438382848 + 3901952, "date": "2026-12-04", "sources_sha1": "64b2b3f734a107711ddfe8d89f779800b3278580"},
+    "pyramid": {"bytes": 63592448 + 203272448 + 15843072 + 10816000 + 3414016 + 0 + 1630208 + 0,
+                "date": "2026-12-04", "sources_sha1": "ff6b931b004ce7541dd969b99393db305a2acc49"},
 }
 KERNEL_SOURCES = {
     "k_klt_batch": ["vt_klt.cuh", "vt_batch.cu", "vt_internal.cuh"],
@@ -132,7 +132,7 @@ def parse():
     ap.add_argument("--served-budget-gb", type=float, default=20.0)
     ap.add_argument("--served-slots", type=int, default=2,
                     help="batches the served loop may have in flight (each on its own CUDA stream)")
-    ap.add_argument("--served-rates", type=lambda v: [float(x) for x in v.split(",")], default=[1, 1.5, 2, 2.5, 3, 4, 8, 16],
+    ap.add_argument("--served-rates", type=lambda v: [float(x) for x in v.split(",")], default=[1, 1.25, 1.5, 1.75, 2, 2.5, 3, 4, 8, 16],
                     help="arrival-rate multipliers of the served sweep (comma-separated)")
     return ap.parse_args()
 
