@@ -474,6 +474,10 @@ def run_native(a, rank, world, local_rank):
     pyr_bytes = sum(pyr_launch_bytes)
     pyr_avg_s = statistics.mean(pyr_ms) / 1e3
     lev_avg_ms = [statistics.mean(x[j] for x in lev_ms) for j in range(len(lev_ms[0]))]
+    lev_names = [f"level {j}" for j in range(len(pyr_launch_bytes) - 1)] + ["tail"]
+    if len(lev_avg_ms) == 2 and len(pyr_launch_bytes) > 2:  # every tiled level in one launch
+        lev_names = [f"levels 0-{len(pyr_launch_bytes) - 2} (one launch)", "tail"]
+        pyr_launch_bytes = [sum(pyr_launch_bytes[:-1]), pyr_launch_bytes[-1]]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -786,7 +790,7 @@ def run_native(a, rank, world, local_rank):
                              / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": pyr_bytes / pyr_avg_s / 1e9 / hbm_peak, "traffic": pyr_traffic,
                              "bytes_per_step": pyr_bytes, "ms": pyr_avg_s * 1e3, "peak_source": hbm_src,
-                             "per_launch": [{"launch": ("tail" if j == len(lev_avg_ms) - 1 else f"level {j}"),
+                             "per_launch": [{"launch": lev_names[j],
                                              "ms": lev_avg_ms[j], "bytes": pyr_launch_bytes[j],
                                              "gbs": pyr_launch_bytes[j] / (lev_avg_ms[j] / 1e3) / 1e9}
                                             for j in range(len(lev_avg_ms))],
