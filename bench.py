@@ -307,6 +307,8 @@ def run_native(a, rank, world, local_rank):
              else None) for i, sp in enumerate(specs)]
     tr = BatchedTracker(specs, prm, grad_type=grad_type, gate=gprm, rigs=rigs, ring=ring)
     last_slot = [0]  # ring slot built by the latest step (every stream alike)
+    free_b, total_b = torch.cuda.mem_get_info()
+    hbm_used_gb = (total_b - free_b) / 1e9  # frame store, ring, pyramids, outputs, context
 
     def step_args(t):
         fp, fc = pingpong(t - 1, F), pingpong(t, F)
@@ -770,6 +772,7 @@ def run_native(a, rank, world, local_rank):
             "l2": "flushed between steps (256 MB write outside the per-step CUDA events)",
             "graph": True,
             "launch_shape": tune,
+            "hbm_used_gb": round(hbm_used_gb, 2),
             "seed": a.seed,
             "parallelism": "replicas" if world > 1 else "single",
         },

@@ -46,6 +46,7 @@ def test_native_small_run_line():
     for sec in ("gftt", "stereo_gate", "track_bookkeeping", "frontend_loop", "plain"):
         assert d[sec], sec
     assert d["config"]["launch_shape"]["warps_per_cta"] in (4, 8)
+    assert 0 < d["config"]["hbm_used_gb"] < 280
 
 
 @pytest.mark.gpu
