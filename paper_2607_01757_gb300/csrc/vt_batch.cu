@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(WARPS * 32, KltOcc<WIN>::min_blocks * 4 / WARP
     k_klt_batch(const uint8_t *tab, int *counter) {
     extern __shared__ __align__(16) uint8_t klt_smem[];
     KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
+    ksmem_init<WIN>(sm, threadIdx.x & 31);
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const BTask *tasks = reinterpret_cast<const BTask *>(tab + H->off_tasks);
     const int *p0s = reinterpret_cast<const int *>(tab + H->off_prefix);
@@ -77,6 +78,7 @@ template <int WIN, int GT>
 __global__ void __launch_bounds__(128) k_klt_batch_f64(const uint8_t *tab) {
     extern __shared__ __align__(16) uint8_t klt_smem[];
     KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
+    ksmem_init<WIN>(sm, threadIdx.x & 31);
     const BatchHdr *H = reinterpret_cast<const BatchHdr *>(tab);
     const BTask *tasks = reinterpret_cast<const BTask *>(tab + H->off_tasks);
     const int *p0s = reinterpret_cast<const int *>(tab + H->off_prefix);

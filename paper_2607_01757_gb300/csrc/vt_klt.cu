@@ -30,6 +30,7 @@ template <int WIN, int GT, bool FB, bool F64>
 __global__ void __launch_bounds__(KLT_WARPS * 32, KltOcc<WIN>::min_blocks) k_klt(const __grid_constant__ KltArgs A) {
     extern __shared__ __align__(16) uint8_t klt_smem[];
     KSmem<WIN> &sm = reinterpret_cast<KSmem<WIN> *>(klt_smem)[threadIdx.x >> 5];
+    ksmem_init<WIN>(sm, threadIdx.x & 31);
     const int pt = blockIdx.x * KLT_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (pt >= A.n) return;

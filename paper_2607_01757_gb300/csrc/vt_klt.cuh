@@ -170,7 +170,22 @@ struct KSmem {
                                                                  "and reads at most 32 bytes past it");
     uint32_t g[(WIN + 1) * GS];
     uint8_t t[(WIN + 1) * JS];  // the template's image window, kept while footprints are staged (FP64 levels)
+    // zeros that a lane's run outside the window reads instead of the staged
+    // windows (its template samples and error terms are then exactly zero
+    // without a select per sample): RL + 1 rows of two bytes / words at the
+    // staged strides (RL = samples per run)
+    static constexpr int RLZ = WIN / (WIN == 31 ? 1 : 3);
+    uint8_t zj[RLZ * JS + 16];
+    uint32_t zg[RLZ * GS + 4];
 };
+
+// Clear a warp's zero rows (once per kernel, before the first point).
+template <int WIN>
+__device__ __forceinline__ void ksmem_init(KSmem<WIN> &sm, int lane) {
+    for (int k = lane; k < (int)sizeof(sm.zj); k += 32) sm.zj[k] = 0;
+    for (int k = lane; k < (int)(sizeof(sm.zg) / 4); k += 32) sm.zg[k] = 0;
+    __syncwarp();
+}
 
 // Which window samples a lane owns.  The win x win window is cut into runs
 // of RL consecutive rows of one column (D bands of RL rows, win * D runs in
@@ -336,8 +351,8 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
         int c, r0;
         bool valid;
         run_of<WIN>(lane, i, c, r0, valid);
-        const uint8_t *jr = &sm.j[r0 * JS + offi + c];
-        const uint32_t *gr = &sm.g[r0 * GS + offg + c];
+        const uint8_t *jr = valid ? &sm.j[r0 * JS + offi + c] : sm.zj;
+        const uint32_t *gr = valid ? &sm.g[r0 * GS + offg + c] : sm.zg;
         float pi = 0.f, pgx = 0.f, pgy = 0.f;
 #pragma unroll
         for (int r = 0; r <= RL; ++r) {
@@ -349,9 +364,9 @@ __device__ __forceinline__ void load_template(const Level &L, float ux, float uy
             const float hgx = fmaf(ax, gxr - gx, gx);
             const float hgy = fmaf(ax, gyr - gy, gy);
             if (r > 0) {
-                T[i * RL + r - 1] = valid ? fmaf(ay, hi - pi, pi) : 0.f;
-                GX[i * RL + r - 1] = valid ? fmaf(ay, hgx - pgx, pgx) : 0.f;
-                GY[i * RL + r - 1] = valid ? fmaf(ay, hgy - pgy, pgy) : 0.f;
+                T[i * RL + r - 1] = fmaf(ay, hi - pi, pi);  // zero for a run outside the window
+                GX[i * RL + r - 1] = fmaf(ay, hgx - pgx, pgx);
+                GY[i * RL + r - 1] = fmaf(ay, hgy - pgy, pgy);
             }
             pi = hi;
             pgx = hgx;
@@ -465,7 +480,7 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
         int c, r0;
         bool valid;
         run_of<WIN>(lane, i, c, r0, valid);
-        const uint8_t *jr = &sm.j[r0 * JS + off + c];
+        const uint8_t *jr = valid ? &sm.j[r0 * JS + off + c] : sm.zj;
         float ph = 0.f;
 #pragma unroll
         for (int r = 0; r <= RL; ++r) {
@@ -473,7 +488,7 @@ __device__ __forceinline__ float abs_residual(const Level &L, float qx, float qy
             const float h = fmaf(bx, u8f(jr[r * JS + 1]) - mv, mv);
             if (r > 0) {
                 const float jv = fmaf(by, h - ph, ph);
-                const float e = valid ? fabsf(T[i * RL + r - 1] - jv) : 0.f;
+                const float e = fabsf(T[i * RL + r - 1] - jv);  // 0 - 0 for a run outside the window
                 if (r & 1)
                     sa += e;
                 else
