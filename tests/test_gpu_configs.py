@@ -301,10 +301,12 @@ def test_stereo_temporal_sequence_64_frames_pool_aging_batched():
     assert max_age >= 20, max_age  # some tracks live through a third of the sequence
 
 
-def test_input_ring_equals_input_slots():
+@pytest.mark.parametrize("grad", ["s16", "f16", "none"])
+def test_input_ring_equals_input_slots(grad):
     """A tracker over an input ring (each slot level 0 of its own pyramid,
     frames never copied) gives bit-identical points, status and errors to the
-    tracker that copies each frame from its input slot, batched and plain."""
+    tracker that copies each frame from its input slot, batched and plain,
+    with int16, half or no stored gradient planes."""
     import torch
 
     import paper_2607_01757_gb300 as vt
@@ -326,8 +328,9 @@ def test_input_ring_equals_input_slots():
     ring = [([slot(f.left[k]) for k in range(F)], [slot(f.right[k]) for k in range(F)] if sp.stereo else None)
             for sp, f in zip(pick, frames)]
     prm = vt.KltParams()
-    tr_r = BatchedTracker(pick, prm, ring=ring)
-    tr_s = BatchedTracker(pick, prm)
+    gt = {"s16": vt.VT_GRAD_S16, "f16": vt.VT_GRAD_F16, "none": vt.VT_GRAD_NONE}[grad]
+    tr_r = BatchedTracker(pick, prm, grad_type=gt, ring=ring)
+    tr_s = BatchedTracker(pick, prm, grad_type=gt)
     sids = list(range(len(pick)))
     dev = lambda a: torch.from_numpy(a).cuda() if a is not None else None  # noqa: E731
     kp = [[dev(f.kps[k]) for k in range(F)] for f in frames]
