@@ -451,7 +451,11 @@ vt_status vt_batch_set(vt_batch *b, const vt_frame_job *frames, int nframes, vt_
                 tiles += nt;
                 ++nj;
             } else {
-                const int parts = tail_parts(p);
+                // bands per frame capped so that every band of the run gets a
+                // CTA of the tail launch in one round
+                const int cap = b->tail_grid / (nframes > 0 ? nframes : 1);
+                int parts = tail_parts(p);
+                if (parts > cap) parts = cap > 1 ? cap : 1;
                 for (int q = 0; q < parts; ++q) {
                     lj[nj].frame = f;
                     lj[nj].tiles_x = q;
